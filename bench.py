@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput of E-field direct imaging (MOFF / EPIC) on an LWA-station-shaped block.
+
+One step = one epic_image call over the station block: 256 dual-pol antennas,
+64 channels spread over 60-76 MHz, 64x64 grid at 0.5-wavelength cells, 5x5
+Gaussian kernel, 1250 samples (50 ms at 40 us), autocorrelations removed --
+every step of the imaging path (unpack, calibrate, grid, 2-D FFT, XX/YY/XY,
+accumulate, autocorrelation removal) in the library's kernels.
+
+Prints one JSON line (rank 0).  Metric: antenna x channel x samples imaged per
+second (whole job).  Inputs are 4 rotating device copies of the block (164 MB,
+larger than L2).  ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded sample of the same block per step.
+
+Multi-GPU (torchrun): every rank images its own block with no collective in the
+data path (channels are independent), so per-GPU work is fixed ("weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "antenna·chan·samples/s imaged, tensor-core vs FP32 path at stated err; %roofline"
+UNIT = "antenna·chan·samples/s"
+# The paper's per-GPU real-time capacity for 256 dual-pol antennas, 64^2 grid,
+# 50 ms gulps: 16 channels x 25 000 samples/s x 256 antennas on a GTX 980.
+PAPER_GTX980 = 16 * 25_000 * 256
+WORKLOAD = ("station: 256 dual-pol antennas in a 110 m disk (min spacing 5 m), 64 channels of 25 kHz "
+            "over 60-76 MHz, 64x64 grid at 0.5 wavelength, 5x5 Gaussian kernel, 1250 samples (50 ms) of "
+            "4+4-bit noise + 3 point sources, XX/YY/XY FP32 images, autocorrelations removed")
+N_COPIES = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="epic", choices=["epic", "reference"])
+    ap.add_argument("--xform", default="fft_fp32")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--soak-seconds", type=float, default=1.5)
+    return ap.parse_args()
+
+
+def fp32_flops_per_tc(A, P, N, S):
+    """Algorithmic FP32 flops of one (time, channel) image set on the FFT path."""
+    import math
+    calib = 6 * A * P                            # complex x integer sample
+    grid = 4 * A * S * S * P                     # real weight x complex, accumulated
+    fft = P * 5 * N * N * int(math.log2(N * N))  # 5 N^2 log2(N^2) per 2-D FFT
+    prod = N * N * (4 if P == 1 else 16)         # |X|^2, |Y|^2, X conj(Y), accumulated
+    return calib + grid + fft + prod
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def src_sha(name):
+    with open(os.path.join(ROOT, "paper_1904_11422_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def dram_traffic(kernel, source):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since it was taken; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        if rec and rec.get("source_sha") == src_sha(source):
+            return rec["bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------
+def cpu_oracle_rate(w, seconds, label="oracle"):
+    """The FP64 oracle (FFT mode, as it stands) on a bounded sample of the block,
+    all host cores.  Returns (units/s, cores, sample description)."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    arr = oracle.OracleArray(w.ant_xy, w.freq_hz, w.n_pol, w.grid_n, w.support, w.cell_lambda, w.sigma_cells)
+    # probe: one sample of `cores` channels
+    n_c = min(cores, w.n_chan)
+    t0 = time.perf_counter()
+    oracle.image(arr, w.volts[:1], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
+    probe = time.perf_counter() - t0
+    n_t = int(max(1, min(w.n_time, seconds / max(probe, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
+    dt = time.perf_counter() - t0
+    units = w.n_ant * n_c * n_t
+    sample = (f"{n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block, "
+              f"FP64 oracle FFT mode with autocorrelation removal, {cores} OpenMP threads, {dt:.1f} s")
+    return units / dt, cores, sample, dt, units
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1904_11422_gb300 import synth
+    w = synth.station()
+    budget = 150.0  # seconds for the whole reference run
+    per_step = max(0.05, budget / max(1, args.steps + args.warmup))
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    arr = oracle.OracleArray(w.ant_xy, w.freq_hz, w.n_pol, w.grid_n, w.support, w.cell_lambda, w.sigma_cells)
+    n_c = min(cores, w.n_chan)
+    t0 = time.perf_counter()
+    oracle.image(arr, w.volts[:1], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
+    probe = time.perf_counter() - t0
+    n_t = int(max(1, min(w.n_time, per_step / max(probe, 1e-4))))
+    step = lambda: oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c,  # noqa: E731
+                                use_fft=True, n_threads=cores)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    units = w.n_ant * n_c * n_t
+    value = units * args.steps / dt
+    sample = (f"per step {n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block, "
+              f"FP64 oracle FFT mode with autocorrelation removal")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_GTX980, "dtype": "f64",
+            "data": "synthetic (seeded, LWA-station-shaped)",
+            "config": {"workload": WORKLOAD, "xform": "oracle FFT mode (FP64, CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1904_11422_gb300 import build_lib, epic, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build_lib.build()
+    if dist is not None:
+        dist.barrier()
+
+    w = synth.station()
+    xform = epic.XFORMS[args.xform]
+    plan = epic.plan_for(w, xform, subtract_autos=True)
+    T = w.n_time
+    copies = [torch.from_numpy(w.volts).cuda() for _ in range(N_COPIES)]
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        epic.epic_image(plan, copies[i % N_COPIES], T, out, 0, stream)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    torch.cuda.synchronize()
+    epic.epic_sync(plan)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    t_soak = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t_soak < args.soak_seconds:  # untimed load, for the clock record
+        step(i)
+        i += 1
+        if i % 50 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+
+    epic.epic_timing_enable(plan, True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kt = epic.epic_timing_read(plan)
+    epic.epic_timing_enable(plan, False)
+    clocks = sampler.stop()
+    epic.epic_sync(plan)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    units_step = w.units
+    value = units_step * args.steps * world / (ms / 1e3)
+
+    # roofline of the dominant kernel
+    pk, pk_kind = peaks()
+    launches = sum(v[0] for v in kt.values())
+    dom = max(kt.items(), key=lambda kv: kv[1][1])[0] if kt else None
+    roof = None
+    if dom == "fft_image":
+        n, tot = kt[dom]
+        avg_s = tot / n / 1e3
+        flops = w.n_chan * T * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": dram_traffic("fft_image", "epic_fft.cu"),
+                "kernel": "fft_image", "kernel_ms": 1e3 * avg_s, "kernel_share": tot / sum(v[1] for v in kt.values()),
+                "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                              f"(max SM clock, {pk_kind})",
+                "flops_per_launch": flops}
+
+    # end to end through the public host-buffer entry point
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = torch.empty(w.volts.shape, dtype=torch.uint8, pin_memory=True)
+        h_in.numpy()[...] = w.volts
+        h_out = torch.empty(plan.out_shape, dtype=torch.float32, pin_memory=True)
+        for _ in range(3):
+            epic.epic_image_host(plan, h_in, T, h_out, 0, stream)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            epic.epic_image_host(plan, h_in, T, h_out, 0, stream)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": units_step * args.e2e_steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(w.volts.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 4),
+               "steps": args.e2e_steps, "api": "epic_image_host (pinned host buffers, synchronous)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, sample, _, _ = cpu_oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    plan.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": value / PAPER_GTX980,
+                "dtype": "f32" if args.xform == "fft_fp32" else args.xform,
+                "data": "synthetic (seeded, LWA-station-shaped; no LWA-SV captures exist here)",
+                "config": {"workload": WORKLOAD, "xform": args.xform, "units_per_step": units_step,
+                           "parallelism": f"channel-independent blocks, one per GPU x {world}",
+                           "l2": f"inputs larger than L2: {N_COPIES} rotating device copies of the block "
+                                 f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kt.items()},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

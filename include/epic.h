@@ -1,0 +1,188 @@
+/*
+ * epic.h -- C ABI of the GB300 E-field direct imager (MOFF / EPIC).
+ *
+ * The library images channelised antenna voltages the way Eq. (5) of Kent et
+ * al. (arxiv 1904.11422) defines it:
+ *
+ *     I(l,m) = < | FT{ W * E' }(l,m) |^2 >
+ *
+ * i.e. unpack 4+4-bit complex samples (Sec. 3.2), apply per-antenna gains and
+ * delay compensation (Sec. 3.2, Fig. 2), grid every antenna through its
+ * illumination kernel W onto a 0.5-wavelength aperture grid (Sec. 3.2-3.3),
+ * spatially Fourier transform each channel and polarisation (Eq. (5), "inverse
+ * FT" in Sec. 3.2), form XX, YY, XY (YX = conj XY), accumulate over the block
+ * (Sec. 2.1, Sec. 3.2) and optionally remove the autocorrelation term (Sec.
+ * 3.2, last paragraph; Fig. 2 "Remove Autocorrelations").
+ *
+ * Conventions shared by every entry point:
+ *   - Plain C types only.  A "stream" argument is a cudaStream_t passed as
+ *     void*; NULL means the legacy default stream.
+ *   - d_* pointers are device memory owned by the caller; h_* pointers are
+ *     host memory owned by the caller.  A plan owns its own device constants
+ *     and workspace and frees them in epic_plan_destroy.
+ *   - Calls that take a stream are asynchronous and stream-ordered.  Argument
+ *     errors are returned synchronously, before anything is launched.
+ *     Launch failures return EPIC_ERR_CUDA.
+ *   - A plan may be used from one stream at a time (its workspace is shared
+ *     by all of its calls).
+ *   - No entry point falls back to a CPU implementation: without a usable
+ *     CUDA device, calls that need one return EPIC_ERR_NO_DEVICE.
+ *
+ * Geometry (fixed by the plan; Sec. 3.2 and the readings stated here):
+ *   - cell size d = cell_lambda wavelengths of each channel;
+ *   - antenna a sits at u = x_a / (lambda_c d) + N/2, v = y_a / (lambda_c d)
+ *     + N/2 cells; its S x S kernel box starts at floor(u + 1/2) - (S-1)/2;
+ *   - kernel: Gaussian exp(-r^2 / (2 sigma^2)) sampled at cell centres, then
+ *     normalised to sum 1 (S = 1: a single unit weight);
+ *   - calibration coefficient k = g * exp(-2 pi i nu tau);
+ *   - output pixel (column i, row j) is direction l = (i - N/2)/(N d),
+ *     m = (j - N/2)/(N d); the transform uses exp(+2 pi i (...)) and no 1/N^2.
+ */
+#ifndef EPIC_H
+#define EPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EPIC_OK = 0,
+  EPIC_ERR_INVALID_ARG = 1, /* a pointer, size or flag is out of range        */
+  EPIC_ERR_OFFGRID = 2,     /* an antenna's kernel box leaves the N x N grid   */
+  EPIC_ERR_UNSUPPORTED = 3, /* valid but not supported (grid size, transform)  */
+  EPIC_ERR_OOM = 4,         /* a device allocation failed                       */
+  EPIC_ERR_CUDA = 5,        /* a CUDA call or launch failed                     */
+  EPIC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up               */
+  EPIC_ERR_NO_DEVICE = 7    /* no usable CUDA device                            */
+} epic_status;
+
+/* How the 2-D spatial transform of Eq. (5) is computed. */
+typedef enum {
+  EPIC_XFORM_FFT_FP32 = 0,   /* shared-memory radix-8 FFT, FP32                 */
+  EPIC_XFORM_DFT_BF16X3 = 1, /* DFT-by-GEMM on tcgen05, BF16 hi+lo (3 products) */
+  EPIC_XFORM_DFT_FP16X3 = 2, /* DFT-by-GEMM on tcgen05, FP16 hi+lo (3 products) */
+  EPIC_XFORM_DFT_BF16 = 3,   /* DFT-by-GEMM on tcgen05, plain BF16              */
+  EPIC_XFORM_DFT_FP16 = 4    /* DFT-by-GEMM on tcgen05, plain FP16              */
+} epic_xform;
+
+/* Everything a plan needs.  epic_plan_create copies every array; the caller
+ * may free them when it returns. */
+typedef struct {
+  int n_ant;                 /* antennas, >= 1                                   */
+  int n_pol;                 /* polarisations: 1 (X) or 2 (X, Y)                 */
+  int n_chan;                /* channels, >= 1                                   */
+  int grid_n;                /* grid side N (power of two, see epic_plan_validate) */
+  int kernel_support;        /* kernel box side S, odd, 1 <= S <= 15, S < N      */
+  double cell_lambda;        /* grid cell in wavelengths, > 0 (0.5 = lambda/2)   */
+  double kernel_sigma_cells; /* Gaussian sigma in cells, > 0 (used when S > 1)   */
+  const double* ant_xy_m;    /* host [n_ant][2]: x (east), y (north) in metres
+                                from the array centre                            */
+  const double* chan_freq_hz;/* host [n_chan]: channel centre frequencies, > 0   */
+  const double* gains;       /* host [n_chan][n_ant][n_pol][2] (re, im) or NULL
+                                for unit gains                                   */
+  const double* delays_s;    /* host [n_ant][n_pol] seconds, or NULL for zero    */
+  int xform;                 /* an epic_xform                                    */
+  int subtract_autos;        /* 1: remove sum_a P_a |W_a(l,m)|^2; 0: raw images */
+} epic_plan_desc;
+
+typedef struct epic_plan epic_plan;
+
+/* Read-only facts about a plan, for callers that size buffers or report. */
+typedef struct {
+  int n_ant, n_pol, n_chan, grid_n, kernel_support, xform, subtract_autos;
+  int device;                /* CUDA device the plan lives on                    */
+  int ctas;                  /* CTAs of one imaging launch                        */
+  int threads_per_cta;       /* threads per CTA of the imaging launch            */
+  size_t device_bytes;       /* device memory held by the plan                   */
+  size_t workspace_bytes;    /* of which per-call scratch (partial images)       */
+  long long max_time;        /* largest n_time accepted by one epic_image call   */
+} epic_plan_info;
+
+/* Host-only check of a descriptor, no CUDA call (the same checks that
+ * epic_plan_create makes before touching the device).  Returns EPIC_OK,
+ * EPIC_ERR_INVALID_ARG (NULL pointer, non-positive or non-finite value, even
+ * or too large support), EPIC_ERR_OFFGRID (some antenna's box leaves the grid
+ * in some channel) or EPIC_ERR_UNSUPPORTED (a grid size or transform this
+ * build does not implement: the FP32 FFT path takes N = 32 or 64 with at most
+ * 2048 antennas). */
+epic_status epic_plan_validate(const epic_plan_desc* desc);
+
+/* Creates a plan on the current CUDA device: validates desc, copies its
+ * arrays, and generates in FP64 on the GPU (Sec. 3.2) each antenna's cell
+ * coordinates, kernel weights, calibration coefficient and kernel power
+ * spectrum |W_a|^2, plus the per-cell gather table of the gridder.  Blocks
+ * until the plan is ready.  *out receives the plan, or NULL on error. */
+epic_status epic_plan_create(const epic_plan_desc* desc, epic_plan** out);
+
+/* Frees a plan and all device memory it holds (synchronises the device).
+ * NULL is accepted. */
+epic_status epic_plan_destroy(epic_plan* plan);
+
+/* Fills *info. */
+epic_status epic_plan_query(const epic_plan* plan, epic_plan_info* info);
+
+/* Images one block of n_time samples (Eq. (5), accumulated over the block).
+ *   d_volts  device [n_time][n_chan][n_ant][n_pol] bytes, one 4+4-bit complex
+ *            sample each (real part in the high nibble, imaginary part in the
+ *            low nibble, 4-bit two's complement).
+ *   n_time   0 <= n_time <= info.max_time.  n_time = 0 images nothing (the
+ *            output is zeroed when accumulate = 0).
+ *   d_out    device [n_chan][4][N][N] float: XX, YY, Re XY, Im XY with
+ *            XY = sum_t Y_X conj(Y_Y); rows are m, columns l.  With one
+ *            polarisation, planes 1-3 are written as zeros.
+ *   accumulate 0: d_out = image; 1: d_out += image.
+ * With subtract_autos the per-antenna term is removed per call, so images are
+ * additive over consecutive blocks.  Deterministic: the same inputs give
+ * bit-identical outputs on the same device.  Uses the plan's workspace. */
+epic_status epic_image(epic_plan* plan, const uint8_t* d_volts, int n_time, float* d_out,
+                       int accumulate, void* stream);
+
+/* The same imaging from host buffers: copies h_volts (host [n_time][n_chan]
+ * [n_ant][n_pol] bytes, pinned or pageable) to a plan-owned device staging
+ * buffer, images it, copies the [n_chan][4][N][N] result to h_out (which is
+ * read first when accumulate = 1) and waits for the stream.  Synchronous. */
+epic_status epic_image_host(epic_plan* plan, const uint8_t* h_volts, int n_time, float* h_out,
+                            int accumulate, void* stream);
+
+/* Waits for the stream and reports any device-side error recorded by the
+ * plan's kernels since the previous call (EPIC_ERR_TIMEOUT, EPIC_ERR_CUDA). */
+epic_status epic_sync(epic_plan* plan, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* epic_status_string(int status);
+
+/* Debug: unpacks n bytes (Sec. 3.2 format above) into d_out [n][2] int8 as
+ * (real, imaginary).  Needs no plan. */
+epic_status epic_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, void* stream);
+
+/* Debug: the gridded, calibrated field G = W * E' (Eq. (5)) of sample t,
+ * channel c, polarisation p of d_volts (layout as in epic_image, n_time
+ * samples), as d_grid [N][N][2] float (row y, column x, re/im), computed with
+ * the imaging kernels' own gather code. */
+epic_status epic_debug_grid(epic_plan* plan, const uint8_t* d_volts, int n_time, int t, int c,
+                            int p, float* d_grid, void* stream);
+
+/* Device time per kernel kind of a plan's launches, for benchmarks. */
+typedef struct {
+  char kernel[32];      /* kernel kind, e.g. "fft_image", "reduce"              */
+  long long launches;   /* launches recorded since timing was enabled          */
+  double total_ms;      /* summed device time of those launches (CUDA events)  */
+} epic_kernel_time;
+
+/* enable = 1: from now on every launch the plan makes is bracketed by CUDA
+ * events on its stream; enable = 0: stop recording.  Both clear the counters.
+ * Recording costs two event records per launch. */
+epic_status epic_timing_enable(epic_plan* plan, int enable);
+
+/* Waits for every recorded launch, then writes up to capacity entries to out
+ * (one per kernel kind seen) and the number of kinds to *count. */
+epic_status epic_timing_read(epic_plan* plan, epic_kernel_time* out, int capacity, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPIC_H */

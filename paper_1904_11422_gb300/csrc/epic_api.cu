@@ -1,0 +1,399 @@
+// epic_api.cu -- the C ABI declared in include/epic.h: validation, plan
+// lifetime, and the launch sequence of one imaging call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "epic_internal.cuh"
+
+using epic::Plan;
+
+struct epic_plan {
+  Plan p;
+};
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr int kMaxAntFft = 2048;
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+// The same FP64 operations, in the same order and each rounded on its own, as
+// the device-side plan kernel (this file is compiled with -ffp-contract=off).
+double cell_coord(double pos_m, double freq_hz, double cell_lambda, int N) {
+  const double lambda = kC0 / freq_hz;
+  return pos_m / (lambda * cell_lambda) + 0.5 * (double)N;
+}
+
+bool grid_supported(int xform, int N) {
+  if (xform == EPIC_XFORM_FFT_FP32) return N == 32 || N == 64;
+  return false;
+}
+
+epic_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return EPIC_OK;
+  if (e == cudaErrorMemoryAllocation) return EPIC_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return EPIC_ERR_NO_DEVICE;
+  return EPIC_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t alloc(T** ptr, size_t count, size_t* total) {
+  *ptr = nullptr;
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * count);
+  if (e == cudaSuccess) *total += sizeof(T) * count;
+  return e;
+}
+
+void free_plan(Plan& p) {
+  for (const Plan::Timed& t : p.pending) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (cudaEvent_t e : p.event_pool) cudaEventDestroy(e);
+  p.pending.clear();
+  p.event_pool.clear();
+  void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
+                  p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
+                  p.d_stage_in, p.d_stage_out};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+// Work units u = c*T + t (channel-major) split into equal contiguous ranges,
+// one per CTA, with no CTA left empty.
+epic::WorkSplit split_work(const Plan& p, int T) {
+  epic::WorkSplit ws;
+  ws.T = T;
+  ws.units = (long long)p.C * T;
+  long long ctas = p.ctas < ws.units ? p.ctas : ws.units;
+  ws.W = (ws.units + ctas - 1) / ctas;
+  ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);
+  return ws;
+}
+
+cudaEvent_t take_event(Plan& p) {
+  if (!p.event_pool.empty()) {
+    cudaEvent_t e = p.event_pool.back();
+    p.event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int kind_index(Plan& p, const char* name) {
+  for (size_t k = 0; k < p.kinds.size(); ++k)
+    if (p.kinds[k] == name) return (int)k;
+  p.kinds.emplace_back(name);
+  p.kind_launches.push_back(0);
+  p.kind_ms.push_back(0.0);
+  return (int)p.kinds.size() - 1;
+}
+
+// Runs launch(), bracketed by events on s when the plan records timing.
+template <class F>
+cudaError_t timed(Plan& p, const char* name, cudaStream_t s, F&& launch) {
+  if (!p.timing) return launch();
+  Plan::Timed t{kind_index(p, name), take_event(p), take_event(p)};
+  cudaEventRecord(t.start, s);
+  cudaError_t e = launch();
+  cudaEventRecord(t.stop, s);
+  p.pending.push_back(t);
+  return e;
+}
+
+cudaError_t drain_timing(Plan& p) {
+  for (const Plan::Timed& t : p.pending) {
+    cudaError_t e = cudaEventSynchronize(t.stop);
+    if (e != cudaSuccess) return e;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.start, t.stop);
+    p.kind_launches[t.kind] += 1;
+    p.kind_ms[t.kind] += ms;
+    p.event_pool.push_back(t.start);
+    p.event_pool.push_back(t.stop);
+  }
+  p.pending.clear();
+  return cudaSuccess;
+}
+
+// Largest number of channels any CTA of a split touches.
+int spans_needed(const epic::WorkSplit& ws) {
+  int worst = 1;
+  for (int b = 0; b < ws.ctas; ++b) {
+    const long long u0 = (long long)b * ws.W;
+    const long long u1 = (u0 + ws.W < ws.units ? u0 + ws.W : ws.units) - 1;
+    const int n = (int)(u1 / ws.T - u0 / ws.T) + 1;
+    if (n > worst) worst = n;
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* epic_status_string(int s) {
+  switch (s) {
+    case EPIC_OK: return "EPIC_OK";
+    case EPIC_ERR_INVALID_ARG: return "EPIC_ERR_INVALID_ARG";
+    case EPIC_ERR_OFFGRID: return "EPIC_ERR_OFFGRID";
+    case EPIC_ERR_UNSUPPORTED: return "EPIC_ERR_UNSUPPORTED";
+    case EPIC_ERR_OOM: return "EPIC_ERR_OOM";
+    case EPIC_ERR_CUDA: return "EPIC_ERR_CUDA";
+    case EPIC_ERR_TIMEOUT: return "EPIC_ERR_TIMEOUT";
+    case EPIC_ERR_NO_DEVICE: return "EPIC_ERR_NO_DEVICE";
+    default: return "EPIC_ERR_UNKNOWN";
+  }
+}
+
+epic_status epic_plan_validate(const epic_plan_desc* d) {
+  if (!d || !d->ant_xy_m || !d->chan_freq_hz) return EPIC_ERR_INVALID_ARG;
+  if (d->n_ant < 1 || d->n_chan < 1 || (d->n_pol != 1 && d->n_pol != 2)) return EPIC_ERR_INVALID_ARG;
+  if (d->n_chan > (1 << 20)) return EPIC_ERR_INVALID_ARG;
+  const int N = d->grid_n, S = d->kernel_support;
+  if (N < 8 || N > 4096 || (N & (N - 1)) != 0) return EPIC_ERR_INVALID_ARG;
+  if (S < 1 || S > 15 || (S % 2) == 0 || S >= N) return EPIC_ERR_INVALID_ARG;
+  if (!is_finite(d->cell_lambda) || d->cell_lambda <= 0.0) return EPIC_ERR_INVALID_ARG;
+  if (S > 1 && (!is_finite(d->kernel_sigma_cells) || d->kernel_sigma_cells <= 0.0)) return EPIC_ERR_INVALID_ARG;
+  if (d->xform < EPIC_XFORM_FFT_FP32 || d->xform > EPIC_XFORM_DFT_FP16) return EPIC_ERR_INVALID_ARG;
+  if (d->subtract_autos != 0 && d->subtract_autos != 1) return EPIC_ERR_INVALID_ARG;
+  const int A = d->n_ant, P = d->n_pol, C = d->n_chan;
+  for (int k = 0; k < 2 * A; ++k)
+    if (!is_finite(d->ant_xy_m[k])) return EPIC_ERR_INVALID_ARG;
+  for (int c = 0; c < C; ++c)
+    if (!is_finite(d->chan_freq_hz[c]) || d->chan_freq_hz[c] <= 0.0) return EPIC_ERR_INVALID_ARG;
+  if (d->gains)
+    for (long long k = 0; k < 2LL * C * A * P; ++k)
+      if (!is_finite(d->gains[k])) return EPIC_ERR_INVALID_ARG;
+  if (d->delays_s)
+    for (int k = 0; k < A * P; ++k)
+      if (!is_finite(d->delays_s[k])) return EPIC_ERR_INVALID_ARG;
+  // every kernel box inside the grid, in every channel (reading R7: no wrap)
+  for (int c = 0; c < C; ++c)
+    for (int a = 0; a < A; ++a) {
+      const double u = cell_coord(d->ant_xy_m[2 * a], d->chan_freq_hz[c], d->cell_lambda, N);
+      const double v = cell_coord(d->ant_xy_m[2 * a + 1], d->chan_freq_hz[c], d->cell_lambda, N);
+      if (!is_finite(u) || !is_finite(v) || std::fabs(u) > 1e9 || std::fabs(v) > 1e9) return EPIC_ERR_OFFGRID;
+      const long long i0 = (long long)std::floor(u + 0.5) - (S - 1) / 2;
+      const long long j0 = (long long)std::floor(v + 0.5) - (S - 1) / 2;
+      if (i0 < 0 || j0 < 0 || i0 + S > N || j0 + S > N) return EPIC_ERR_OFFGRID;
+    }
+  if (!grid_supported(d->xform, N)) return EPIC_ERR_UNSUPPORTED;
+  if (d->xform == EPIC_XFORM_FFT_FP32 && A > kMaxAntFft) return EPIC_ERR_UNSUPPORTED;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
+  if (!out) return EPIC_ERR_INVALID_ARG;
+  *out = nullptr;
+  epic_status st = epic_plan_validate(d);
+  if (st != EPIC_OK) return st;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return from_cuda(e);
+  epic_plan* h = new (std::nothrow) epic_plan();
+  if (!h) return EPIC_ERR_OOM;
+  Plan& p = h->p;
+  p.A = d->n_ant; p.P = d->n_pol; p.C = d->n_chan; p.N = d->grid_n; p.S = d->kernel_support;
+  p.xform = d->xform; p.subtract = d->subtract_autos;
+  p.cell_lambda = d->cell_lambda;
+  p.sigma = p.S > 1 ? d->kernel_sigma_cells : 1.0;
+  p.device = dev;
+  cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev);
+
+  const size_t A = p.A, P = p.P, C = p.C, N = p.N, S = p.S;
+  size_t total = 0;
+  auto fail = [&](cudaError_t err) {
+    free_plan(p);
+    delete h;
+    return from_cuda(err);
+  };
+#define EPIC_TRY(x)                   \
+  do {                                \
+    cudaError_t err_ = (x);           \
+    if (err_ != cudaSuccess) return fail(err_); \
+  } while (0)
+  EPIC_TRY(alloc(&p.d_ant_xy, 2 * A, &total));
+  EPIC_TRY(alloc(&p.d_freq, C, &total));
+  if (d->gains) EPIC_TRY(alloc(&p.d_gains, 2 * C * A * P, &total));
+  if (d->delays_s) EPIC_TRY(alloc(&p.d_delays, A * P, &total));
+  EPIC_TRY(alloc(&p.d_box, 2 * C * A, &total));
+  EPIC_TRY(alloc(&p.d_wx, C * A * S, &total));
+  EPIC_TRY(alloc(&p.d_wy, C * A * S, &total));
+  EPIC_TRY(alloc(&p.d_coef, C * A * P, &total));
+  EPIC_TRY(alloc(&p.d_coef64, C * A * P, &total));
+  EPIC_TRY(alloc(&p.d_kx2, C * A * N, &total));
+  EPIC_TRY(alloc(&p.d_ky2, C * A * N, &total));
+  EPIC_TRY(alloc(&p.d_csr_ptr, C * (N * N + 1), &total));
+  EPIC_TRY(alloc(&p.d_csr_ent, C * A * S * S, &total));
+  EPIC_TRY(alloc(&p.d_twiddle, N, &total));
+  EPIC_TRY(alloc(&p.d_status, 1, &total));
+
+  EPIC_TRY(cudaMemcpy(p.d_ant_xy, d->ant_xy_m, sizeof(double) * 2 * A, cudaMemcpyHostToDevice));
+  EPIC_TRY(cudaMemcpy(p.d_freq, d->chan_freq_hz, sizeof(double) * C, cudaMemcpyHostToDevice));
+  if (d->gains) EPIC_TRY(cudaMemcpy(p.d_gains, d->gains, sizeof(double) * 2 * C * A * P, cudaMemcpyHostToDevice));
+  if (d->delays_s) EPIC_TRY(cudaMemcpy(p.d_delays, d->delays_s, sizeof(double) * A * P, cudaMemcpyHostToDevice));
+  EPIC_TRY(cudaMemset(p.d_status, 0, sizeof(int)));
+
+  EPIC_TRY(epic::launch_plan_terms(p, 0));
+  EPIC_TRY(epic::launch_twiddles(p, 0));
+  EPIC_TRY(epic::launch_build_csr(p, 0));
+  EPIC_TRY(cudaDeviceSynchronize());
+  int status = 0, nnz_last = 0;
+  EPIC_TRY(cudaMemcpy(&status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status == epic::kDevOffGrid) {
+    free_plan(p);
+    delete h;
+    return EPIC_ERR_OFFGRID;
+  }
+  // every antenna contributes S*S entries to every channel's gather table
+  for (size_t c = 0; c < C; ++c) {
+    EPIC_TRY(cudaMemcpy(&nnz_last, p.d_csr_ptr + c * (N * N + 1) + N * N, sizeof(int), cudaMemcpyDeviceToHost));
+    if ((size_t)nnz_last != A * S * S) return fail(cudaErrorUnknown);
+  }
+
+  int per_sm = 0;
+  EPIC_TRY(epic::fft_image_config(p, &per_sm));
+  if (per_sm < 1) return fail(cudaErrorInvalidConfiguration);
+  p.ctas = p.sm_count * per_sm;
+  p.spans = (p.C + p.ctas - 1) / p.ctas + 2;
+  size_t before = total;
+  EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * N * N, &total));
+  EPIC_TRY(alloc(&p.d_part_auto, (size_t)p.ctas * p.spans * A * 4, &total));
+  p.workspace_bytes = total - before;
+  p.device_bytes = total;
+#undef EPIC_TRY
+  *out = h;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_destroy(epic_plan* h) {
+  if (!h) return EPIC_OK;
+  cudaDeviceSynchronize();
+  free_plan(h->p);
+  delete h;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_query(const epic_plan* h, epic_plan_info* info) {
+  if (!h || !info) return EPIC_ERR_INVALID_ARG;
+  const Plan& p = h->p;
+  info->n_ant = p.A; info->n_pol = p.P; info->n_chan = p.C; info->grid_n = p.N;
+  info->kernel_support = p.S; info->xform = p.xform; info->subtract_autos = p.subtract;
+  info->device = p.device; info->ctas = p.ctas; info->threads_per_cta = p.threads;
+  info->device_bytes = p.device_bytes + p.stage_in_bytes + (p.d_stage_out ? sizeof(float) * 4 * p.C * p.N * p.N : 0);
+  info->workspace_bytes = p.workspace_bytes;
+  // integer self powers stay exact in int32 per CTA and the unit index in int64
+  info->max_time = (1LL << 24);
+  return EPIC_OK;
+}
+
+epic_status epic_image(epic_plan* h, const uint8_t* d_volts, int n_time, float* d_out, int accumulate,
+                       void* stream) {
+  if (!h || !d_out || n_time < 0 || n_time > (1 << 24) || (accumulate != 0 && accumulate != 1))
+    return EPIC_ERR_INVALID_ARG;
+  if (n_time > 0 && !d_volts) return EPIC_ERR_INVALID_ARG;
+  Plan& p = h->p;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t out_n = (size_t)p.C * 4 * p.N * p.N;
+  if (n_time == 0) return accumulate ? EPIC_OK : from_cuda(epic::launch_zero(d_out, out_n, s));
+  const epic::WorkSplit ws = split_work(p, n_time);
+  if (spans_needed(ws) > p.spans) return EPIC_ERR_CUDA;  // cannot happen: spans sized for any n_time
+  cudaError_t e = timed(p, "fft_image", s, [&] { return epic::launch_fft_image(p, d_volts, n_time, ws, s); });
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(timed(p, "reduce", s, [&] { return epic::launch_reduce(p, n_time, ws, d_out, accumulate, s); }));
+}
+
+epic_status epic_image_host(epic_plan* h, const uint8_t* h_volts, int n_time, float* h_out, int accumulate,
+                            void* stream) {
+  if (!h || !h_out || n_time < 0 || n_time > (1 << 24) || (accumulate != 0 && accumulate != 1))
+    return EPIC_ERR_INVALID_ARG;
+  if (n_time > 0 && !h_volts) return EPIC_ERR_INVALID_ARG;
+  Plan& p = h->p;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t in_bytes = (size_t)n_time * p.C * p.A * p.P;
+  const size_t out_bytes = sizeof(float) * (size_t)p.C * 4 * p.N * p.N;
+  if (in_bytes > p.stage_in_bytes) {
+    if (p.d_stage_in) cudaFree(p.d_stage_in);
+    p.d_stage_in = nullptr;
+    p.stage_in_bytes = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p.d_stage_in), in_bytes);
+    if (e != cudaSuccess) return from_cuda(e);
+    p.stage_in_bytes = in_bytes;
+  }
+  if (!p.d_stage_out) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p.d_stage_out), out_bytes);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  cudaError_t e = cudaSuccess;
+  if (in_bytes) e = cudaMemcpyAsync(p.d_stage_in, h_volts, in_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && accumulate) e = cudaMemcpyAsync(p.d_stage_out, h_out, out_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  epic_status st = epic_image(h, p.d_stage_in, n_time, p.d_stage_out, accumulate, stream);
+  if (st != EPIC_OK) return st;
+  e = cudaMemcpyAsync(h_out, p.d_stage_out, out_bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+epic_status epic_sync(epic_plan* h, void* stream) {
+  if (!h) return EPIC_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return from_cuda(e);
+  int status = 0;
+  e = cudaMemcpy(&status, h->p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (status == epic::kDevOk) return EPIC_OK;
+  cudaMemset(h->p.d_status, 0, sizeof(int));
+  return status == epic::kDevTimeout ? EPIC_ERR_TIMEOUT : EPIC_ERR_CUDA;
+}
+
+epic_status epic_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, void* stream) {
+  if (n > 0 && (!d_in || !d_out)) return EPIC_ERR_INVALID_ARG;
+  return from_cuda(epic::launch_debug_unpack(d_in, n, d_out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+epic_status epic_debug_grid(epic_plan* h, const uint8_t* d_volts, int n_time, int t, int c, int p, float* d_grid,
+                            void* stream) {
+  if (!h || !d_volts || !d_grid || n_time < 1 || t < 0 || t >= n_time || c < 0 || c >= h->p.C || p < 0 ||
+      p >= h->p.P)
+    return EPIC_ERR_INVALID_ARG;
+  return from_cuda(epic::launch_debug_grid(h->p, d_volts, n_time, t, c, p, d_grid,
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
+epic_status epic_timing_enable(epic_plan* h, int enable) {
+  if (!h || (enable != 0 && enable != 1)) return EPIC_ERR_INVALID_ARG;
+  Plan& p = h->p;
+  cudaError_t e = drain_timing(p);
+  for (size_t k = 0; k < p.kinds.size(); ++k) {
+    p.kind_launches[k] = 0;
+    p.kind_ms[k] = 0.0;
+  }
+  p.timing = enable != 0;
+  return from_cuda(e);
+}
+
+epic_status epic_timing_read(epic_plan* h, epic_kernel_time* out, int capacity, int* count) {
+  if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return EPIC_ERR_INVALID_ARG;
+  Plan& p = h->p;
+  cudaError_t e = drain_timing(p);
+  if (e != cudaSuccess) return from_cuda(e);
+  *count = (int)p.kinds.size();
+  for (int k = 0; k < capacity && k < (int)p.kinds.size(); ++k) {
+    std::memset(out[k].kernel, 0, sizeof(out[k].kernel));
+    std::strncpy(out[k].kernel, p.kinds[k].c_str(), sizeof(out[k].kernel) - 1);
+    out[k].launches = p.kind_launches[k];
+    out[k].total_ms = p.kind_ms[k];
+  }
+  return EPIC_OK;
+}
+
+}  // extern "C"

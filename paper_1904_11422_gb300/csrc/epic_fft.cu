@@ -1,0 +1,441 @@
+// epic_fft.cu -- the FP32 imaging path: one fused kernel per block that unpacks,
+// calibrates, grids, transforms and squares, accumulating images on chip.
+//
+// Per work unit (time sample t of channel c), following Eq. (5) and Sec. 3.2:
+//   1. unpack the A x P bytes of (t, c) (4+4-bit complex, Sec. 3.2), multiply by
+//      the calibration coefficient k (delay compensation and gain, Fig. 2) and
+//      accumulate each antenna's self power (Fig. 2 "Accumulate
+//      Autocorrelations") exactly, on the integer samples;
+//   2. grid: every cell gathers w * e from the antennas whose kernel box covers
+//      it (the convolution W * E' of Eq. (5)), atomics-free and in a fixed order;
+//   3. transform: 2-D FFT with the exp(+2 pi i ...) kernel of Eq. (5) ("inverse
+//      FT", Sec. 3.2), as radix-8 passes: rows in registers with a warp-local
+//      exchange, one CTA-wide transpose through shared memory, columns likewise;
+//   4. square and cross-multiply (XX, YY, XY; Sec. 2.1, Fig. 2 "Square and
+//      Accumulate") into per-thread register accumulators that stay resident
+//      for the CTA's whole span of samples.
+// The grid of one (t, c) never leaves the SM.  A CTA owns a contiguous range of
+// (c, t) units (channel-major) and writes one partial image per channel it
+// touches; a separate kernel sums partials in CTA order and removes the
+// autocorrelation term.
+#include "epic_internal.cuh"
+
+namespace epic {
+
+namespace {
+
+constexpr int kMaxAnt = 2048;
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+
+// 4-point DFT with the exp(+2 pi i nk/4) kernel; natural order in and out.
+__device__ __forceinline__ void dft4(float2& y0, float2& y1, float2& y2, float2& y3) {
+  const float2 s02 = cadd(y0, y2), d02 = csub(y0, y2);
+  const float2 s13 = cadd(y1, y3), d13 = mul_i(csub(y1, y3));
+  y0 = cadd(s02, s13);
+  y2 = csub(s02, s13);
+  y1 = cadd(d02, d13);
+  y3 = csub(d02, d13);
+}
+
+// 8-point DFT with the exp(+2 pi i nk/8) kernel: one radix-2 split into even
+// and odd outputs, then two 4-point DFTs.  Natural order in and out.
+__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+  const float h = 0.70710678118654752f;  // 1/sqrt(2)
+  float2 a0 = cadd(x[0], x[4]), a1 = cadd(x[1], x[5]), a2 = cadd(x[2], x[6]), a3 = cadd(x[3], x[7]);
+  float2 b0 = csub(x[0], x[4]);
+  const float2 t1 = csub(x[1], x[5]);
+  float2 b1 = make_float2(h * (t1.x - t1.y), h * (t1.x + t1.y));   // * exp(+i pi/4)
+  float2 b2 = mul_i(csub(x[2], x[6]));                             // * exp(+i pi/2)
+  const float2 t3 = csub(x[3], x[7]);
+  float2 b3 = make_float2(-h * (t3.x + t3.y), h * (t3.x - t3.y));  // * exp(+3i pi/4)
+  dft4(a0, a1, a2, a3);
+  dft4(b0, b1, b2, b3);
+  x[0] = a0; x[2] = a1; x[4] = a2; x[6] = a3;
+  x[1] = b0; x[3] = b1; x[5] = b2; x[7] = b3;
+}
+
+// Thread geometry of an N-point line transform: R1 threads per line, 8 points
+// per thread (element n1 + R1*n2 held by thread n1 as its n2-th value).
+// swz/scr are XOR layouts checked to be free of shared-memory bank conflicts
+// for every access pattern below.
+template <int N> struct Geo;
+template <> struct Geo<64> {
+  static constexpr int R1 = 8, THREADS = 512, RPW = 4, SCR = 4 * 72;
+  __device__ static int swz(int y) { return (9 * (y & 7)) & 15; }
+  __device__ static int scr(int r, int k2, int n1) { return r * 72 + k2 * 8 + (n1 ^ k2); }
+  // output index held as value s by thread q after a line transform
+  __host__ __device__ static constexpr int kidx(int q, int s) { return q + 8 * s; }
+};
+template <> struct Geo<32> {
+  static constexpr int R1 = 4, THREADS = 128, RPW = 8, SCR = 8 * 36;
+  __device__ static int swz(int y) { return (5 * (y & 7)) & 15; }
+  __device__ static int scr(int r, int k2, int n1) { return r * 36 + k2 * 4 + (n1 ^ ((k2 >> 1) & 3)); }
+  __host__ __device__ static constexpr int kidx(int q, int s) { return 2 * q + (s >> 2) + 8 * (s & 3); }
+};
+
+// One N-point transform of a line held by R1 threads (Cooley-Tukey N = R1 x 8):
+// 8-point DFT over n2, twiddle exp(+2 pi i n1 k2 / N), exchange through warp
+// scratch, then the R1-point DFT over n1.  On return thread q holds output
+// Geo<N>::kidx(q, s) as v[s].
+template <int N>
+__device__ __forceinline__ void fft_line(float2 (&v)[8], const float2 (&tw)[8], float2* __restrict__ scr, int r,
+                                         int n1) {
+  using G = Geo<N>;
+  dft8(v);
+#pragma unroll
+  for (int k2 = 1; k2 < 8; ++k2) v[k2] = cmul(v[k2], tw[k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) scr[G::scr(r, k2, n1)] = v[k2];
+  __syncwarp();
+  if constexpr (N == 64) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = scr[G::scr(r, n1, m)];
+    dft8(v);
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v[4 * h + m] = scr[G::scr(r, 2 * n1 + h, m)];
+    dft4(v[0], v[1], v[2], v[3]);
+    dft4(v[4], v[5], v[6], v[7]);
+  }
+  __syncwarp();
+}
+
+// Shared-memory layout of the imaging kernel, in bytes from the base.
+struct FftSmem {
+  size_t R, scr, ptr, coef, E, autos, ent, total;
+};
+
+template <int N, int P>
+__host__ __device__ inline FftSmem fft_smem_layout(int A, int nnz, int ent_in_smem) {
+  using G = Geo<N>;
+  FftSmem L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 15) & ~(size_t)15;
+    return at;
+  };
+  L.R = take(sizeof(float2) * P * N * N);
+  L.scr = take(sizeof(float2) * (G::THREADS / 32) * G::SCR);
+  L.ptr = take(sizeof(int) * (N * N + 1));
+  L.coef = take(sizeof(float2) * A * P);
+  L.E = take((P == 2 ? 16 : 8) * (size_t)A);
+  L.autos = take(sizeof(int4) * A);
+  L.ent = take(ent_in_smem ? sizeof(int2) * (size_t)nnz : 0);
+  L.total = o;
+  return L;
+}
+
+template <int N, int P>
+__global__ void __launch_bounds__(Geo<N>::THREADS, 1)
+    fft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
+                     const float2* __restrict__ coef, const int* __restrict__ csr_ptr,
+                     const int2* __restrict__ csr_ent, int nnz, int ent_in_smem,
+                     const float2* __restrict__ twiddle, float* __restrict__ part, int* __restrict__ part_auto) {
+  using G = Geo<N>;
+  constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2;
+  constexpr int MAXK = (kMaxAnt + NT - 1) / NT;
+  constexpr int NPL = (P == 2) ? 4 : 1;
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const FftSmem L = fft_smem_layout<N, P>(A, nnz, ent_in_smem);
+  float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
+  float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
+  int* ptr_s = reinterpret_cast<int*>(smem + L.ptr);
+  float2* coef_s = reinterpret_cast<float2*>(smem + L.coef);
+  float4* E4 = reinterpret_cast<float4*>(smem + L.E);
+  float2* E2 = reinterpret_cast<float2*>(smem + L.E);
+  int4* auto_s = reinterpret_cast<int4*>(smem + L.autos);
+  int2* ent_s = reinterpret_cast<int2*>(smem + L.ent);
+
+  const int tid = threadIdx.x;
+  const int line = tid / R1, n1 = tid % R1, r = line % G::RPW;
+
+  float2 tw[8];
+  tw[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[(n1 * k2) & (N - 1)];
+
+  const long long u0 = (long long)blockIdx.x * W;
+  const long long u1 = min(u0 + W, units);
+  if (u0 >= u1) return;
+  const int c_first = (int)(u0 / T);
+
+  float acc[NPL][8];
+#pragma unroll
+  for (int pl = 0; pl < NPL; ++pl)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
+
+  // raw bytes of the thread's antennas, prefetched one unit ahead
+  unsigned raw[MAXK] = {}, raw_next[MAXK] = {};
+  auto load_raw = [&](long long u, unsigned (&dst)[MAXK]) {
+    const int c = (int)(u / T), t = (int)(u % T);
+    const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k) {
+      const int a = tid + k * NT;
+      if (a < A) {
+        if constexpr (P == 2)
+          dst[k] = __ldg(reinterpret_cast<const unsigned short*>(base) + a);
+        else
+          dst[k] = __ldg(base + a);
+      }
+    }
+  };
+  load_raw(u0, raw);
+
+  int cur_c = -1;
+  const int2* ent = csr_ent;
+
+  auto flush = [&](int c) {
+    const int slot = c - c_first;
+    float* dst = part + (size_t)((long long)blockIdx.x * spans + slot) * 4 * NN;
+    // thread (column k = line, q = n1) holds pixel rows kidx(q, s); shift so that
+    // pixel N/2 is the zero frequency (reading R4)
+    const int col = (line + HALF) & (N - 1);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int row = (G::kidx(n1, s) + HALF) & (N - 1);
+#pragma unroll
+      for (int pl = 0; pl < NPL; ++pl) dst[(size_t)pl * NN + row * N + col] = acc[pl][s];
+    }
+    int4* pa = reinterpret_cast<int4*>(part_auto) + (size_t)((long long)blockIdx.x * spans + slot) * A;
+    for (int a = tid; a < A; a += NT) pa[a] = auto_s[a];
+  };
+
+  for (long long u = u0; u < u1; ++u) {
+    const int c = (int)(u / T);
+    if (c != cur_c) {
+      if (cur_c >= 0) {
+        flush(cur_c);
+#pragma unroll
+        for (int pl = 0; pl < NPL; ++pl)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
+      }
+      cur_c = c;
+      const int* cp = csr_ptr + (size_t)c * (NN + 1);
+      for (int k = tid; k <= NN; k += NT) ptr_s[k] = cp[k];
+      for (int k = tid; k < A * P; k += NT) coef_s[k] = coef[(size_t)c * A * P + k];
+      for (int a = tid; a < A; a += NT) auto_s[a] = make_int4(0, 0, 0, 0);
+      if (ent_in_smem) {
+        const int2* src = csr_ent + (size_t)c * nnz;
+        for (int k = tid; k < nnz; k += NT) ent_s[k] = src[k];
+        ent = ent_s;
+      } else {
+        ent = csr_ent + (size_t)c * nnz;
+      }
+      __syncthreads();
+    }
+    if (u + 1 < u1) load_raw(u + 1, raw_next);
+
+    // 1. unpack, calibrate, exact integer self powers
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k) {
+      const int a = tid + k * NT;
+      if (a < A) {
+        const int xr = nib_hi(raw[k] & 0xffu), xi = nib_lo(raw[k] & 0xffu);
+        const float2 kx = coef_s[a * P];
+        const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
+        int4 au = auto_s[a];
+        au.x += xr * xr + xi * xi;
+        if constexpr (P == 2) {
+          const int yr = nib_hi(raw[k] >> 8), yi = nib_lo(raw[k] >> 8);
+          const float2 ky = coef_s[a * P + 1];
+          const float2 ey = make_float2(ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
+          E4[a] = make_float4(ex.x, ex.y, ey.x, ey.y);
+          au.y += yr * yr + yi * yi;
+          au.z += xr * yr + xi * yi;
+          au.w += xi * yr - xr * yi;
+        } else {
+          E2[a] = ex;
+        }
+        auto_s[a] = au;
+      }
+    }
+    __syncthreads();
+
+    // 2. grid (gather, fixed order) and 3a. row transforms; thread (row y, n1)
+    {
+      const int y = line;
+      float2 v[P][8];
+#pragma unroll
+      for (int n2 = 0; n2 < 8; ++n2) {
+        const int cell = y * N + n1 + R1 * n2;
+        const int e0 = ptr_s[cell], e1 = ptr_s[cell + 1];
+        float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
+        for (int e = e0; e < e1; ++e) {
+          const int2 en = ent[e];
+          const float w = __int_as_float(en.y);
+          if constexpr (P == 2) {
+            const float4 ev = E4[en.x];
+            gx.x = fmaf(w, ev.x, gx.x);
+            gx.y = fmaf(w, ev.y, gx.y);
+            gy.x = fmaf(w, ev.z, gy.x);
+            gy.y = fmaf(w, ev.w, gy.y);
+          } else {
+            const float2 ev = E2[en.x];
+            gx.x = fmaf(w, ev.x, gx.x);
+            gx.y = fmaf(w, ev.y, gx.y);
+          }
+        }
+        v[0][n2] = gx;
+        if constexpr (P == 2) v[1][n2] = gy;
+      }
+      const int sw = G::swz(y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        fft_line<N>(v[p], tw, scr, r, n1);
+        float2* Rrow = Rbuf + (size_t)p * NN + y * N;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) Rrow[G::kidx(n1, s) ^ sw] = v[p][s];
+      }
+    }
+    __syncthreads();
+
+    // 3b. column transforms and 4. products; thread (column k, m1)
+    {
+      const int k = line;
+      float2 v[P][8];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int m2 = 0; m2 < 8; ++m2) {
+          const int y = n1 + R1 * m2;
+          v[p][m2] = Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))];
+        }
+        fft_line<N>(v[p], tw, scr, r, n1);
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float2 X = v[0][s];
+        acc[0][s] = fmaf(X.x, X.x, fmaf(X.y, X.y, acc[0][s]));
+        if constexpr (P == 2) {
+          const float2 Y = v[1][s];
+          acc[1][s] = fmaf(Y.x, Y.x, fmaf(Y.y, Y.y, acc[1][s]));
+          acc[2][s] = fmaf(X.x, Y.x, fmaf(X.y, Y.y, acc[2][s]));
+          acc[3][s] = fmaf(X.y, Y.x, fmaf(-X.x, Y.y, acc[3][s]));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < MAXK; ++k) raw[k] = raw_next[k];
+  }
+  flush(cur_c);
+}
+
+template <int N, int P>
+cudaError_t set_attrs(size_t smem) {
+  return cudaFuncSetAttribute(fft_image_kernel<N, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int N, int P>
+cudaError_t occupancy(int threads, size_t smem, int* per_sm) {
+  cudaError_t e = set_attrs<N, P>(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fft_image_kernel<N, P>, threads, smem);
+}
+
+size_t smem_for(const Plan& p, int ent_in_smem) {
+  const int nnz = p.A * p.S * p.S;
+  if (p.N == 64) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, nnz, ent_in_smem).total
+                                 : fft_smem_layout<64, 1>(p.A, nnz, ent_in_smem).total;
+  return p.P == 2 ? fft_smem_layout<32, 2>(p.A, nnz, ent_in_smem).total
+                  : fft_smem_layout<32, 1>(p.A, nnz, ent_in_smem).total;
+}
+
+bool ent_fits(const Plan& p) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return smem_for(p, 1) <= (size_t)optin;
+}
+
+// The gridding step alone, for the debug entry point: the same gather table,
+// entry order and FP32 fused multiply-adds as the imaging kernel.
+template <int P>
+__global__ void debug_grid_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, int N, int t, int c, int pol,
+                                  const float2* __restrict__ coef, const int* __restrict__ csr_ptr,
+                                  const int2* __restrict__ csr_ent, int nnz, float* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* E = reinterpret_cast<float2*>(smem);
+  const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
+  for (int a = threadIdx.x; a < A; a += blockDim.x) {
+    const unsigned b = base[a * P + pol];
+    const int re = nib_hi(b), im = nib_lo(b);
+    const float2 k = coef[((size_t)c * A + a) * P + pol];
+    E[a] = make_float2(k.x * re - k.y * im, k.x * im + k.y * re);
+  }
+  __syncthreads();
+  const int* ptr = csr_ptr + (size_t)c * (N * N + 1);
+  const int2* ent = csr_ent + (size_t)c * nnz;
+  for (int cell = threadIdx.x; cell < N * N; cell += blockDim.x) {
+    float2 g = make_float2(0.f, 0.f);
+    for (int e = ptr[cell]; e < ptr[cell + 1]; ++e) {
+      const int2 en = ent[e];
+      const float w = __int_as_float(en.y);
+      const float2 ev = E[en.x];
+      g.x = fmaf(w, ev.x, g.x);
+      g.y = fmaf(w, ev.y, g.y);
+    }
+    grid[2 * cell] = g.x;
+    grid[2 * cell + 1] = g.y;
+  }
+}
+
+}  // namespace
+
+cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
+  p.ent_in_smem = ent_fits(p) ? 1 : 0;
+  p.smem = smem_for(p, p.ent_in_smem);
+  p.threads = (p.N == 64) ? Geo<64>::THREADS : Geo<32>::THREADS;
+  if (p.N == 64) return p.P == 2 ? occupancy<64, 2>(p.threads, p.smem, ctas_per_sm)
+                                 : occupancy<64, 1>(p.threads, p.smem, ctas_per_sm);
+  return p.P == 2 ? occupancy<32, 2>(p.threads, p.smem, ctas_per_sm)
+                  : occupancy<32, 1>(p.threads, p.smem, ctas_per_sm);
+}
+
+cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s) {
+  const int nnz = p.A * p.S * p.S;
+  const int ent = p.ent_in_smem;
+#define EPIC_LAUNCH(NN_, PP_)                                                                                   \
+  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, \
+                                                                 p.d_coef, p.d_csr_ptr, p.d_csr_ent, nnz, ent,  \
+                                                                 p.d_twiddle, p.d_part, p.d_part_auto)
+  if (p.N == 64) {
+    if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
+  } else {
+    if (p.P == 2) EPIC_LAUNCH(32, 2); else EPIC_LAUNCH(32, 1);
+  }
+#undef EPIC_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol, float* d_grid,
+                              cudaStream_t s) {
+  const int nnz = p.A * p.S * p.S;
+  const size_t smem = sizeof(float2) * p.A;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(p.P == 2 ? debug_grid_kernel<2> : debug_grid_kernel<1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (p.P == 2)
+    debug_grid_kernel<2><<<1, 256, smem, s>>>(d_volts, T, p.C, p.A, p.N, t, c, pol, p.d_coef, p.d_csr_ptr,
+                                              p.d_csr_ent, nnz, d_grid);
+  else
+    debug_grid_kernel<1><<<1, 256, smem, s>>>(d_volts, T, p.C, p.A, p.N, t, c, pol, p.d_coef, p.d_csr_ptr,
+                                              p.d_csr_ent, nnz, d_grid);
+  return cudaGetLastError();
+}
+
+}  // namespace epic

@@ -1,0 +1,106 @@
+// epic_internal.cuh -- plan layout and kernel launchers shared by the .cu files
+// of libepic.so.  Not part of the public ABI (include/epic.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/epic.h"
+
+namespace epic {
+
+// Device-side error word values (written by kernels, read by epic_sync).
+enum : int { kDevOk = 0, kDevTimeout = 1, kDevBadIndex = 2, kDevOffGrid = 3 };
+
+// Per-CTA channel spans: CTA b of an imaging launch owns the work units
+// [b*W, min((b+1)*W, C*T)) of the channel-major (c, t) index u = c*T + t.
+struct WorkSplit {
+  int ctas;        // CTAs of the launch
+  long long units; // C * T
+  long long W;     // units per CTA
+  int T;
+};
+
+struct Plan {
+  // descriptor copy
+  int A, P, C, N, S, xform, subtract;
+  double cell_lambda, sigma;
+  int device, sm_count;
+
+  // plan constants, generated on the GPU in FP64 (Sec. 3.2)
+  double* d_ant_xy = nullptr;   // [A][2]
+  double* d_freq = nullptr;     // [C]
+  double* d_gains = nullptr;    // [C][A][P][2] (or null)
+  double* d_delays = nullptr;   // [A][P] (or null)
+  int* d_box = nullptr;         // [C][A][2] kernel box origin (i0, j0)
+  double* d_wx = nullptr;       // [C][A][S] normalised 1-D kernel factors along x
+  double* d_wy = nullptr;       // [C][A][S] along y
+  float2* d_coef = nullptr;     // [C][A][P] calibration coefficient k (FP32)
+  double2* d_coef64 = nullptr;  // [C][A][P] the same in FP64
+  float* d_kx2 = nullptr;       // [C][A][N] |FT of w_x|^2 per output column
+  float* d_ky2 = nullptr;       // [C][A][N] |FT of w_y|^2 per output row
+  int* d_csr_ptr = nullptr;     // [C][N*N+1] gather table: cell -> entries
+  int2* d_csr_ent = nullptr;    // [C][A*S*S] (antenna, weight bits), antenna order
+  float2* d_twiddle = nullptr;  // [N] exp(+2 pi i m / N)
+  int* d_status = nullptr;      // device error word
+
+  // imaging launch shape and its workspace (partial images per CTA span)
+  int ctas = 0, threads = 0, spans = 0, ent_in_smem = 0;
+  size_t smem = 0;
+  float* d_part = nullptr;      // [ctas][spans][4][N][N]
+  int* d_part_auto = nullptr;   // [ctas][spans][A][4] exact integer self powers
+  size_t device_bytes = 0, workspace_bytes = 0;
+
+  // optional per-launch timing (epic_timing_enable)
+  struct Timed {
+    int kind;
+    cudaEvent_t start, stop;
+  };
+  bool timing = false;
+  std::vector<std::string> kinds;
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<long long> kind_launches;
+  std::vector<double> kind_ms;
+
+  // staging for epic_image_host
+  uint8_t* d_stage_in = nullptr;
+  size_t stage_in_bytes = 0;
+  float* d_stage_out = nullptr;
+};
+
+// ---- launchers (each returns cudaGetLastError() of its launch) -------------
+cudaError_t launch_plan_terms(Plan& p, cudaStream_t s);
+cudaError_t launch_build_csr(Plan& p, cudaStream_t s);
+cudaError_t launch_twiddles(Plan& p, cudaStream_t s);
+
+// FP32 FFT path: the fused unpack + calibrate + grid + FFT + products kernel.
+// Sets p.threads, p.smem, p.ent_in_smem and returns the resident CTAs per SM.
+cudaError_t fft_image_config(Plan& p, int* ctas_per_sm);
+cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws,
+                             cudaStream_t s);
+
+// Block end: sum the CTA partials of every channel in a fixed order, remove the
+// autocorrelation term, write or accumulate the output.
+cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int accumulate,
+                          cudaStream_t s);
+cudaError_t launch_zero(float* d_out, size_t n, cudaStream_t s);
+
+cudaError_t launch_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, cudaStream_t s);
+cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol,
+                              float* d_grid, cudaStream_t s);
+
+// ---- small device helpers shared by the kernels ----------------------------
+// Sec. 3.2: one byte = 4-bit real (high nibble) + 4-bit imaginary (low nibble),
+// both two's complement.
+__device__ __forceinline__ int nib_hi(unsigned b) { return (int)((b >> 4) & 15u) - (int)((b >> 3) & 16u); }
+__device__ __forceinline__ int nib_lo(unsigned b) { return (int)(b & 15u) - (int)((b << 1) & 16u); }
+
+__host__ __device__ __forceinline__ long long span_first_unit(const WorkSplit& ws, int b) {
+  return (long long)b * ws.W;
+}
+
+}  // namespace epic
