@@ -142,26 +142,40 @@ def dram_traffic(kernel, source):
 
 
 # --------------------------------------------------------------------------
-def cpu_oracle_rate(w, seconds, label="oracle"):
-    """The FP64 oracle (FFT mode, as it stands) on a bounded sample of the block,
-    all host cores.  Returns (units/s, cores, sample description)."""
+def _oracle_setup(w):
     import oracle
     oracle.build()
-    cores = oracle.max_threads()
     arr = oracle.OracleArray(w.ant_xy, w.freq_hz, w.n_pol, w.grid_n, w.support, w.cell_lambda, w.sigma_cells)
-    # probe: one sample of `cores` channels
-    n_c = min(cores, w.n_chan)
-    t0 = time.perf_counter()
-    oracle.image(arr, w.volts[:1], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
-    probe = time.perf_counter() - t0
-    n_t = int(max(1, min(w.n_time, seconds / max(probe, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
-    dt = time.perf_counter() - t0
+    return oracle, arr, oracle.max_threads()
+
+
+def _oracle_sample(oracle, arr, w, cores, target_s):
+    """Grow a sample of the block (channels first up to the core count, then
+    samples, then more channels) until one oracle run takes about target_s.
+    Returns (n_chan, n_time, seconds of the last run)."""
+    n_c, n_t = min(cores, w.n_chan), 1
+    while True:
+        t0 = time.perf_counter()
+        oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= 0.8 * target_s or (n_t == w.n_time and n_c == w.n_chan):
+            return n_c, n_t, dt
+        grow = max(2.0, min(8.0, target_s / max(dt, 1e-3)))
+        if n_t < w.n_time:
+            n_t = min(w.n_time, int(n_t * grow) + 1)
+        else:
+            n_c = min(w.n_chan, int(n_c * grow) + 1)
+
+
+def cpu_oracle_rate(w, seconds):
+    """The FP64 oracle (FFT mode, as it stands) on a bounded sample of the block,
+    all host cores.  Returns (units/s, cores, sample description)."""
+    oracle, arr, cores = _oracle_setup(w)
+    n_c, n_t, dt = _oracle_sample(oracle, arr, w, cores, seconds)
     units = w.n_ant * n_c * n_t
     sample = (f"{n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block, "
               f"FP64 oracle FFT mode with autocorrelation removal, {cores} OpenMP threads, {dt:.1f} s")
-    return units / dt, cores, sample, dt, units
+    return units / dt, cores, sample
 
 
 def run_reference(args):
@@ -171,18 +185,13 @@ def run_reference(args):
     from paper_1904_11422_gb300 import synth
     w = synth.station()
     budget = 150.0  # seconds for the whole reference run
-    per_step = max(0.05, budget / max(1, args.steps + args.warmup))
-    import oracle
-    oracle.build()
-    cores = oracle.max_threads()
-    arr = oracle.OracleArray(w.ant_xy, w.freq_hz, w.n_pol, w.grid_n, w.support, w.cell_lambda, w.sigma_cells)
-    n_c = min(cores, w.n_chan)
-    t0 = time.perf_counter()
-    oracle.image(arr, w.volts[:1], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
-    probe = time.perf_counter() - t0
-    n_t = int(max(1, min(w.n_time, per_step / max(probe, 1e-4))))
-    step = lambda: oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c,  # noqa: E731
-                                use_fft=True, n_threads=cores)
+    per_step = max(0.2, budget / max(1, args.steps + args.warmup))
+    oracle, arr, cores = _oracle_setup(w)
+    n_c, n_t, _ = _oracle_sample(oracle, arr, w, cores, per_step)
+
+    def step():
+        oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
+
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
@@ -192,7 +201,7 @@ def run_reference(args):
     units = w.n_ant * n_c * n_t
     value = units * args.steps / dt
     sample = (f"per step {n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block, "
-              f"FP64 oracle FFT mode with autocorrelation removal")
+              f"FP64 oracle FFT mode with autocorrelation removal, {cores} OpenMP threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_GTX980, "dtype": "f64",
@@ -324,7 +333,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, cores, sample, _, _ = cpu_oracle_rate(w, args.cpu_seconds)
+        rate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     plan.close()
