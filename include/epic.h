@@ -147,6 +147,35 @@ epic_status epic_image(epic_plan* plan, const uint8_t* d_volts, int n_time, floa
 epic_status epic_image_host(epic_plan* plan, const uint8_t* h_volts, int n_time, float* h_out,
                             int accumulate, void* stream);
 
+/* Size of the static device array that epic_image_noalloc takes its scratch
+ * space from (32 MiB, held on every GPU that loads the library until exit). */
+#define EPIC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* epic_image for callers that must not allocate device memory while they run:
+ * for example a real-time streaming loop, where an allocation can stall on
+ * device-wide synchronisation and break the block's time budget, or a host
+ * application that accounts for all device memory through its own allocator.
+ * (The paper has no counterpart; it is an interface addition.)
+ * Same arguments, layouts and results as epic_image (FP32 FFT plans only;
+ * otherwise EPIC_ERR_UNSUPPORTED), computed by the same kernels with the same
+ * summation order, but the per-call scratch (partial images and self powers)
+ * comes from one static device array of EPIC_NOALLOC_SCRATCH_BYTES instead of
+ * the plan's workspace, and no call allocates anything.
+ *   - The plan's scratch need (epic_plan_info.workspace_bytes, rounded up to
+ *     256-byte pieces) must fit in EPIC_NOALLOC_SCRATCH_BYTES; a plan that needs
+ *     more is rejected with EPIC_ERR_UNSUPPORTED before anything is launched.
+ *   - The plan's device must be the current device (else EPIC_ERR_INVALID_ARG).
+ *   - The first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress, which may load the library's device code); make that
+ *     first call before any stream capture and before the time-critical loop.
+ *   - Every call, from every plan and stream, shares the one array: calls that
+ *     overlap on the GPU race and corrupt each other's results.  Order them on
+ *     one stream or synchronise between them.  The array keeps the previous
+ *     call's contents; each call writes every slot it reads, so nothing needs
+ *     clearing. */
+epic_status epic_image_noalloc(epic_plan* plan, const uint8_t* d_volts, int n_time, float* d_out,
+                               int accumulate, void* stream);
+
 /* Waits for the stream and reports any device-side error recorded by the
  * plan's kernels since the previous call (EPIC_ERR_TIMEOUT, EPIC_ERR_CUDA). */
 epic_status epic_sync(epic_plan* plan, void* stream);

@@ -10,10 +10,6 @@
 
 using epic::Plan;
 
-struct epic_plan {
-  Plan p;
-};
-
 namespace {
 
 constexpr double kC0 = 299792458.0;

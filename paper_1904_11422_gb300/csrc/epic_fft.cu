@@ -420,6 +420,23 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
   return cudaGetLastError();
 }
 
+cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
+                                int* part_auto, cudaStream_t s) {
+  const int nnz = p.A * p.S * p.S;
+  const int ent = p.ent_in_smem;
+#define EPIC_LAUNCH(NN_, PP_)                                                                                   \
+  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, \
+                                                                 p.d_coef, p.d_csr_ptr, p.d_csr_ent, nnz, ent,  \
+                                                                 p.d_twiddle, part, part_auto)
+  if (p.N == 64) {
+    if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
+  } else {
+    if (p.P == 2) EPIC_LAUNCH(32, 2); else EPIC_LAUNCH(32, 1);
+  }
+#undef EPIC_LAUNCH
+  return cudaGetLastError();
+}
+
 cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol, float* d_grid,
                               cudaStream_t s) {
   const int nnz = p.A * p.S * p.S;

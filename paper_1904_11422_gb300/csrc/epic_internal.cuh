@@ -89,6 +89,14 @@ cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int
                           cudaStream_t s);
 cudaError_t launch_zero(float* d_out, size_t n, cudaStream_t s);
 
+// The same two launches with the partial-image workspace passed explicitly
+// (used by the entry point that allocates nothing and takes its workspace from
+// a static device array).
+cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
+                                int* part_auto, cudaStream_t s);
+cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const float* part, const int* part_auto,
+                             float* d_out, int accumulate, cudaStream_t s);
+
 cudaError_t launch_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, cudaStream_t s);
 cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol,
                               float* d_grid, cudaStream_t s);
@@ -104,3 +112,8 @@ __host__ __device__ __forceinline__ long long span_first_unit(const WorkSplit& w
 }
 
 }  // namespace epic
+
+// The opaque handle of include/epic.h.
+struct epic_plan {
+  epic::Plan p;
+};

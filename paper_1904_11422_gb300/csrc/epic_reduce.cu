@@ -116,6 +116,22 @@ cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const float* part, const int* part_auto,
+                             float* d_out, int accumulate, cudaStream_t s) {
+  int rows = 1;
+  while (rows * p.N < kReduceThreads && rows < p.N) rows *= 2;
+  const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
+  auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(p.C, p.N / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, p.spans, p.subtract, accumulate, rows,
+                                        part, part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero(float* d_out, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const size_t blocks = (n + 255) / 256;

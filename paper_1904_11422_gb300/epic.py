@@ -73,6 +73,7 @@ SIGNATURES = {
     "epic_plan_query": (_I, [_P, ctypes.POINTER(epic_plan_info)]),
     "epic_image": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_image_host": (_I, [_P, _P, _I, _P, _I, _P]),
+    "epic_image_noalloc": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_sync": (_I, [_P, _P]),
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
@@ -234,6 +235,18 @@ def epic_image(plan: Plan, d_volts, n_time: int, d_out, accumulate: int = 0, str
     o = _dev_tensor(d_out, "float32", "d_out")
     _check(load_library().epic_image(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
            "epic_image")
+
+
+def epic_image_noalloc(plan: Plan, d_volts, n_time: int, d_out, accumulate: int = 0, stream=None) -> None:
+    """epic_image without any device allocation: scratch from the library's static
+    device array (EPIC_NOALLOC_SCRATCH_BYTES); calls that overlap on the GPU race."""
+    v = _dev_tensor(d_volts, "uint8", "d_volts") if d_volts is not None else None
+    o = _dev_tensor(d_out, "float32", "d_out")
+    _check(load_library().epic_image_noalloc(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
+           "epic_image_noalloc")
+
+
+EPIC_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def epic_image_host(plan: Plan, h_volts, n_time: int, h_out, accumulate: int = 0, stream=None) -> None:
