@@ -24,9 +24,12 @@ double cell_coord(double pos_m, double freq_hz, double cell_lambda, int N) {
   return pos_m / (lambda * cell_lambda) + 0.5 * (double)N;
 }
 
-bool grid_supported(int xform, int N) {
-  if (xform == EPIC_XFORM_FFT_FP32) return N == 32 || N == 64;
-  return false;
+constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA on sm_100/sm_103 (227 KB)
+
+bool grid_supported(int xform, int N, int P, int A, int S) {
+  if (xform == EPIC_XFORM_FFT_FP32) return (N == 32 || N == 64) && A <= kMaxAntFft;
+  // tensor path: 64 x 64 grids of two polarisations, gather table in shared memory
+  return N == 64 && P == 2 && epic::dft_smem_need(A, S) <= kSmemOptin;
 }
 
 epic_status from_cuda(cudaError_t e) {
@@ -55,7 +58,7 @@ void free_plan(Plan& p) {
   p.event_pool.clear();
   void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
                   p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
-                  p.d_stage_in, p.d_stage_out};
+                  p.d_stage_in, p.d_stage_out, p.d_fmat, p.d_ptr9};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -181,8 +184,7 @@ epic_status epic_plan_validate(const epic_plan_desc* d) {
       const long long j0 = (long long)std::floor(v + 0.5) - (S - 1) / 2;
       if (i0 < 0 || j0 < 0 || i0 + S > N || j0 + S > N) return EPIC_ERR_OFFGRID;
     }
-  if (!grid_supported(d->xform, N)) return EPIC_ERR_UNSUPPORTED;
-  if (d->xform == EPIC_XFORM_FFT_FP32 && A > kMaxAntFft) return EPIC_ERR_UNSUPPORTED;
+  if (!grid_supported(d->xform, N, P, A, S)) return EPIC_ERR_UNSUPPORTED;
   return EPIC_OK;
 }
 
@@ -256,7 +258,15 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   }
 
   int per_sm = 0;
-  EPIC_TRY(epic::fft_image_config(p, &per_sm));
+  if (p.xform == EPIC_XFORM_FFT_FP32) {
+    EPIC_TRY(epic::fft_image_config(p, &per_sm));
+  } else {
+    EPIC_TRY(alloc(&p.d_fmat, (size_t)4 * 128 * 128 / 2, &total));
+    EPIC_TRY(alloc(&p.d_ptr9, C * 9 * 512, &total));
+    EPIC_TRY(epic::launch_dft_tables(p, 0));
+    EPIC_TRY(cudaDeviceSynchronize());
+    EPIC_TRY(epic::dft_image_config(p, &per_sm));
+  }
   if (per_sm < 1) return fail(cudaErrorInvalidConfiguration);
   p.ctas = p.sm_count * per_sm;
   p.spans = (p.C + p.ctas - 1) / p.ctas + 2;
@@ -302,7 +312,11 @@ epic_status epic_image(epic_plan* h, const uint8_t* d_volts, int n_time, float* 
   if (n_time == 0) return accumulate ? EPIC_OK : from_cuda(epic::launch_zero(d_out, out_n, s));
   const epic::WorkSplit ws = split_work(p, n_time);
   if (spans_needed(ws) > p.spans) return EPIC_ERR_CUDA;  // cannot happen: spans sized for any n_time
-  cudaError_t e = timed(p, "fft_image", s, [&] { return epic::launch_fft_image(p, d_volts, n_time, ws, s); });
+  cudaError_t e = (p.xform == EPIC_XFORM_FFT_FP32)
+                      ? timed(p, "fft_image", s, [&] { return epic::launch_fft_image(p, d_volts, n_time, ws, s); })
+                      : timed(p, "dft_image", s, [&] {
+                          return epic::launch_dft_image(p, d_volts, n_time, ws, p.d_part, p.d_part_auto, s);
+                        });
   if (e != cudaSuccess) return from_cuda(e);
   return from_cuda(timed(p, "reduce", s, [&] { return epic::launch_reduce(p, n_time, ws, d_out, accumulate, s); }));
 }

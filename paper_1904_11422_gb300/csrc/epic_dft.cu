@@ -1,0 +1,562 @@
+// epic_dft.cu -- the tensor-core imaging path: the 2-D transform of Eq. (5) as
+// two dense real GEMMs on tcgen05, fused with unpack, gridding, squaring and
+// accumulation in one kernel per imaging call.
+//
+// With F[k][x] = exp(+2 pi i (k - N/2) x / N) (the pixel shift of reading R4
+// folded into the rows), one (t, c) image set is Y_g = F G_g F^T for the two
+// polarisation grids g.  Each complex product is one real GEMM on the 2N x 2N
+// matrix [[Fr, -Fi], [Fi, Fr]] (rows interleaved re/im):
+//   stage 1 (along x): D1[(g,y)][(k,c)]  = sum_(c',x) G[(g,y)][(c',x)] Fre[(k,c)][(c',x)]
+//   stage 2 (along y): D2[(j,c)][(g,k)]  = sum_(c',y) Fre[(j,c)][(c',y)] Z[(g,k)][(c',y)]
+// with Z the stage-1 result moved from TMEM to shared memory.  At N = 64 both are
+// M = N = K = 128 GEMMs, A and B K-major in 128-byte-swizzled shared memory, the
+// FP32 accumulators in tensor memory.  The operands are split into a high and a
+// low 16-bit part (BF16 or FP16) and three products hi.hi + hi.lo + lo.hi are
+// accumulated (the "x3" transforms), or only the high parts are used.
+//
+// One elected thread issues the MMAs and commits them to an mbarrier; every wait
+// on it is bounded (about one second) and reports EPIC_ERR_TIMEOUT through the
+// plan's status word instead of hanging.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "epic_internal.cuh"
+
+namespace epic {
+
+namespace {
+
+constexpr int kN = 64;               // grid side of this kernel
+constexpr int kThreads = 512;        // 16 warps
+constexpr int kTmemCols = 256;       // D1 at columns [0,128), D2 at [128,256)
+constexpr int kSlab = 128 * 128;     // one 128-row x 64-element 16-bit operand slab, bytes
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bounded waits: one second
+
+// ---- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 consecutive 32-bit TMEM columns of the warp's 32 lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Shared-memory matrix descriptor, K-major operand with the 128-byte swizzle:
+// 8-row x 128-byte atoms (1024 B) stacked along M/N (stride 1024 B).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;             // leading-dimension offset (unused by this layout)
+  d |= (uint64_t)(1024u >> 4) << 32;   // stride between 8-row groups
+  d |= (uint64_t)1u << 46;             // descriptor version for tcgen05
+  d |= (uint64_t)2u << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B K-major, M = N = 128.
+template <bool kBf16>
+__host__ __device__ constexpr uint32_t idesc_m128n128() {
+  return (1u << 4) | ((kBf16 ? 1u : 0u) << 7) | ((kBf16 ? 1u : 0u) << 10) | ((128u >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+
+// Byte offset of element (row r, k in [0,64)) inside a 128-row swizzled slab.
+__host__ __device__ __forceinline__ uint32_t slab_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+// 16-bit operand type of a transform and its hi/lo split.
+template <int XF> struct Prec;
+template <> struct Prec<EPIC_XFORM_DFT_BF16X3> {
+  using T = __nv_bfloat16;
+  static constexpr bool kBf16 = true, kSplit = true;
+};
+template <> struct Prec<EPIC_XFORM_DFT_FP16X3> {
+  using T = __half;
+  static constexpr bool kBf16 = false, kSplit = true;
+};
+template <> struct Prec<EPIC_XFORM_DFT_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr bool kBf16 = true, kSplit = false;
+};
+template <> struct Prec<EPIC_XFORM_DFT_FP16> {
+  using T = __half;
+  static constexpr bool kBf16 = false, kSplit = false;
+};
+
+template <bool kBf16>
+__device__ __forceinline__ unsigned short to16(float v) {
+  if constexpr (kBf16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  else return __half_as_ushort(__float2half_rn(v));
+}
+template <bool kBf16>
+__device__ __forceinline__ float from16(unsigned short h) {
+  if constexpr (kBf16) return __bfloat162float(__ushort_as_bfloat16(h));
+  else return __half2float(__ushort_as_half(h));
+}
+
+// Shared memory of the kernel (offsets from a 1024-byte aligned base).
+struct DftSmem {
+  static constexpr uint32_t F = 0;                // 4 slabs: hi K0-63, hi K64-127, lo K0-63, lo K64-127
+  static constexpr uint32_t AB = 4 * kSlab;       // 4 slabs: the gridded fields (stage-1 A), then Z (stage-2 B)
+  static constexpr uint32_t E = 8 * kSlab;        // [A] float4 calibrated fields
+};
+
+template <int XF>
+__global__ void __launch_bounds__(kThreads, 1)
+    dft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
+                     const float2* __restrict__ coef, const int* __restrict__ ptr9, const int* __restrict__ csr_ptr,
+                     const int2* __restrict__ csr_ent, int nnz, const uint4* __restrict__ fmat,
+                     float* __restrict__ part, int* __restrict__ part_auto, int* __restrict__ status) {
+  using Pr = Prec<XF>;
+  constexpr int NN = kN * kN;
+  constexpr uint32_t kIdesc = idesc_m128n128<Pr::kBf16>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzle atoms
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  unsigned char* sm = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(sm);
+  float4* E4 = reinterpret_cast<float4*>(sm + DftSmem::E);
+  float2* coef_s = reinterpret_cast<float2*>(E4 + A);       // [A][2]
+  int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A);    // [A]
+  int2* ent_s = reinterpret_cast<int2*>(auto_s + A);         // [nnz]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(ent_s + nnz);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long u0 = (long long)blockIdx.x * W;
+  const long long u1 = min(u0 + W, units);
+  if (u0 >= u1) return;
+  const int c_first = (int)(u0 / T);
+
+  // ---- one-time set-up: TMEM, mbarrier, the DFT matrix in shared memory ----
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    tmem_relinquish();
+    tc_fence_before();
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(bar), 1);
+    fence_mbar_init();
+    *abort_flag = 0;
+  }
+  {
+    uint4* dstF = reinterpret_cast<uint4*>(sm + DftSmem::F);
+    for (int k = tid; k < 4 * kSlab / 16; k += kThreads) dstF[k] = fmat[k];
+  }
+  fence_proxy_async();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_d1 = tmem, tmem_d2 = tmem + 128;
+  uint32_t phase = 0, pending = 0;
+
+  // thread roles for the CUDA-core phases
+  const int gy = tid >> 3, gq = tid & 7;                  // gridder: row y, cells x = 8q..8q+7
+  const int lg = warp & 3, cq = warp >> 2;                // TMEM lane group, column quarter
+  // epilogue: lanes (j, c) = (16*lg + lane/2, lane&1); columns k in [16 cq, 16 cq + 16) of both grids
+  const int ej = 16 * lg + (lane >> 1), ec = lane & 1;
+
+  float acc[4][8];
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
+
+  int cur_c = -1;
+  int p9[9];
+  auto flush = [&](int c) {
+    const int slot = c - c_first;
+    float* dst = part + (size_t)((long long)blockIdx.x * spans + slot) * 4 * NN;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int k = 16 * cq + 8 * ec + s;
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) dst[(size_t)pl * NN + ej * kN + k] = acc[pl][s];
+    }
+    int4* pa = reinterpret_cast<int4*>(part_auto) + (size_t)((long long)blockIdx.x * spans + slot) * A;
+    for (int a = tid; a < A; a += kThreads) pa[a] = auto_s[a];
+  };
+
+  for (long long u = u0; u < u1; ++u) {
+    const int c = (int)(u / T), t = (int)(u % T);
+    if (c != cur_c) {
+      if (cur_c >= 0) {
+        flush(cur_c);
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
+      }
+      cur_c = c;
+      for (int k = tid; k < 2 * A; k += kThreads) coef_s[k] = coef[(size_t)c * A * 2 + k];
+      for (int a = tid; a < A; a += kThreads) auto_s[a] = make_int4(0, 0, 0, 0);
+      const int2* src = csr_ent + (size_t)c * nnz;
+      for (int k = tid; k < nnz; k += kThreads) ent_s[k] = src[k];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) p9[j] = ptr9[((size_t)c * 9 + j) * kThreads + tid];
+      __syncthreads();
+    }
+
+    // 1. unpack, calibrate, exact integer self powers
+    {
+      const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * 2;
+      for (int a = tid; a < A; a += kThreads) {
+        const unsigned raw = __ldg(reinterpret_cast<const unsigned short*>(base) + a);
+        const int xr = nib_hi(raw & 0xffu), xi = nib_lo(raw & 0xffu);
+        const int yr = nib_hi(raw >> 8), yi = nib_lo(raw >> 8);
+        const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
+        E4[a] = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
+                            ky.x * yi + ky.y * yr);
+        int4 au = auto_s[a];
+        au.x += xr * xr + xi * xi;
+        au.y += yr * yr + yi * yi;
+        au.z += xr * yr + xi * yi;
+        au.w += xi * yr - xr * yi;
+        auto_s[a] = au;
+      }
+    }
+    __syncthreads();
+
+    // 2. grid 8 cells (y, 8q..8q+7) of both polarisations and store them, split
+    //    into 16-bit hi/lo parts, as rows (g, y) of the stage-1 A operand
+    {
+      float gre[2][8], gim[2][8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
+        for (int e = p9[s]; e < p9[s + 1]; ++e) {
+          const int2 en = ent_s[e];
+          const float w = __int_as_float(en.y);
+          const float4 ev = E4[en.x];
+          xr = fmaf(w, ev.x, xr);
+          xi = fmaf(w, ev.y, xi);
+          yr = fmaf(w, ev.z, yr);
+          yi = fmaf(w, ev.w, yi);
+        }
+        gre[0][s] = xr; gim[0][s] = xi; gre[1][s] = yr; gim[1][s] = yi;
+      }
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int row = g * kN + gy;
+        const uint32_t off = slab_off(row, 8 * gq);
+#pragma unroll
+        for (int comp = 0; comp < 2; ++comp) {
+          const float* v = comp ? gim[g] : gre[g];
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const unsigned short h0 = to16<Pr::kBf16>(v[2 * s]), h1 = to16<Pr::kBf16>(v[2 * s + 1]);
+            hi[s] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            if constexpr (Pr::kSplit) {
+              const unsigned short l0 = to16<Pr::kBf16>(v[2 * s] - from16<Pr::kBf16>(h0));
+              const unsigned short l1 = to16<Pr::kBf16>(v[2 * s + 1] - from16<Pr::kBf16>(h1));
+              lo[s] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+          }
+          *reinterpret_cast<uint4*>(sm + DftSmem::AB + comp * kSlab + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          if constexpr (Pr::kSplit)
+            *reinterpret_cast<uint4*>(sm + DftSmem::AB + (2 + comp) * kSlab + off) =
+                make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    // 3. stage 1: D1 = A1 . Fre^T (3 or 1 products, K = 128 in steps of 16)
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t aHi = sbase + DftSmem::AB, aLo = aHi + 2 * kSlab;
+      const uint32_t fHi = sbase + DftSmem::F, fLo = fHi + 2 * kSlab;
+      uint32_t accum = 0;
+#pragma unroll
+      for (int pr = 0; pr < (Pr::kSplit ? 3 : 1); ++pr) {
+        const uint32_t a = (pr == 2) ? aLo : aHi;
+        const uint32_t b = (pr == 1) ? fLo : fHi;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint32_t koff = (kk >> 2) * kSlab + (kk & 3) * 32;
+          mma_f16(tmem_d1, sdesc_sw128(a + koff), sdesc_sw128(b + koff), kIdesc, accum);
+          accum = 1;
+        }
+      }
+      mma_commit(smem_u32(bar));
+    }
+    if (!mbar_wait_bounded(smem_u32(bar), phase)) {
+      atomicExch(status, kDevTimeout);
+      *abort_flag = 1;
+    }
+    pending = phase;
+    phase ^= 1;
+    tc_fence_after();
+
+    // 4. Z = D1 (TMEM lanes (g, y), columns (k, c)) -> stage-2 B operand rows
+    //    (g, k), K = (c, y), split hi/lo; warp covers lanes 32 lg.., k in [16 cq, +16)
+    {
+      const int g = lg >> 1, y = 32 * (lg & 1) + lane;
+      float v[2][16];
+      tmem_ld16(tmem_d1 + ((uint32_t)(32 * lg) << 16) + 32 * cq, v[0]);
+      tmem_ld16(tmem_d1 + ((uint32_t)(32 * lg) << 16) + 32 * cq + 16, v[1]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int k = 16 * cq + 8 * h + s;
+          const int row = g * kN + k;
+#pragma unroll
+          for (int comp = 0; comp < 2; ++comp) {
+            const float val = v[h][2 * s + comp];
+            const unsigned short hi = to16<Pr::kBf16>(val);
+            const uint32_t off = slab_off(row, y);
+            *reinterpret_cast<unsigned short*>(sm + DftSmem::AB + comp * kSlab + off) = hi;
+            if constexpr (Pr::kSplit)
+              *reinterpret_cast<unsigned short*>(sm + DftSmem::AB + (2 + comp) * kSlab + off) =
+                  to16<Pr::kBf16>(val - from16<Pr::kBf16>(hi));
+          }
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag) break;
+
+    // 5. stage 2: D2 = Fre . Z^T
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t zHi = sbase + DftSmem::AB, zLo = zHi + 2 * kSlab;
+      const uint32_t fHi = sbase + DftSmem::F, fLo = fHi + 2 * kSlab;
+      uint32_t accum = 0;
+#pragma unroll
+      for (int pr = 0; pr < (Pr::kSplit ? 3 : 1); ++pr) {
+        const uint32_t a = (pr == 2) ? fLo : fHi;
+        const uint32_t b = (pr == 1) ? zLo : zHi;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint32_t koff = (kk >> 2) * kSlab + (kk & 3) * 32;
+          mma_f16(tmem_d2, sdesc_sw128(a + koff), sdesc_sw128(b + koff), kIdesc, accum);
+          accum = 1;
+        }
+      }
+      mma_commit(smem_u32(bar));
+    }
+    if (!mbar_wait_bounded(smem_u32(bar), phase)) {
+      atomicExch(status, kDevTimeout);
+      *abort_flag = 1;
+    }
+    pending = phase;
+    phase ^= 1;
+    tc_fence_after();
+
+    // 6. products: D2 lanes (j, c), columns (g, k); pair lanes 2j / 2j+1 exchange
+    //    the other component, each keeps 8 of the warp's 16 columns
+    {
+      float X[16], Y[16];
+      tmem_ld16(tmem_d2 + ((uint32_t)(32 * lg) << 16) + 16 * cq, X);
+      tmem_ld16(tmem_d2 + ((uint32_t)(32 * lg) << 16) + 64 + 16 * cq, Y);
+      tmem_wait_ld();
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        // lane c = 0 keeps k = s (sends its real parts of k = 8 + s); c = 1 keeps k = 8 + s
+        const float sx = ec ? X[s] : X[8 + s], sy = ec ? Y[s] : Y[8 + s];
+        const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
+        const float xr = ec ? rx : X[s], xi = ec ? X[8 + s] : rx;
+        const float yr = ec ? ry : Y[s], yi = ec ? Y[8 + s] : ry;
+        acc[0][s] = fmaf(xr, xr, fmaf(xi, xi, acc[0][s]));
+        acc[1][s] = fmaf(yr, yr, fmaf(yi, yi, acc[1][s]));
+        acc[2][s] = fmaf(xr, yr, fmaf(xi, yi, acc[2][s]));
+        acc[3][s] = fmaf(xi, yr, fmaf(-xr, yi, acc[3][s]));
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag) break;
+  }
+  if (cur_c >= 0 && !*abort_flag) flush(cur_c);
+  // after a timed-out wait the MMAs may still be running: give them one more
+  // bounded wait before the tensor memory they write is released
+  if (*abort_flag) mbar_wait_bounded(smem_u32(bar), pending);
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---- plan-time tables ----------------------------------------------------------
+// The real 2N x 2N DFT matrix, rows m = 2k + c (c = 0 real, 1 imaginary output
+// part), columns K = c' N + x, split hi/lo in FP64 and written as the byte image
+// of the four shared-memory slabs the kernel copies.
+template <bool kBf16>
+__global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
+  const int m = blockIdx.x;          // 0..127
+  const int kk = threadIdx.x;        // 0..127
+  const int k = m >> 1, c = m & 1, cp = kk >> 6, x = kk & 63;
+  const int f = k - kN / 2;
+  const int ph = (((f * x) % kN) + kN) % kN;
+  double sn, cs;
+  sincospi(2.0 * (double)ph / (double)kN, &sn, &cs);
+  // [[Fr, -Fi], [Fi, Fr]]: output re = Fr*Gr - Fi*Gi ; output im = Fi*Gr + Fr*Gi
+  const double v = (c == 0) ? (cp == 0 ? cs : -sn) : (cp == 0 ? sn : cs);
+  uint16_t hi, lo;
+  if (kBf16) {
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
+  } else {
+    const __half h = __double2half(v);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__double2half(v - (double)__half2float(h)));
+  }
+  const uint32_t off = slab_off(m, x) / 2;
+  out[(size_t)(0 * 2 + cp) * (kSlab / 2) + off] = hi;
+  out[(size_t)(1 * 2 + cp) * (kSlab / 2) + off] = lo;
+}
+
+// Thread-major row pointers of the gridder: thread (y, q) owns cells
+// (y, 8q .. 8q+7); entry j of its list is the CSR pointer of cell 8q + j.
+__global__ void ptr9_kernel(int C, const int* __restrict__ csr_ptr, int* __restrict__ ptr9) {
+  const int c = blockIdx.x, tid = threadIdx.x;
+  const int y = tid >> 3, q = tid & 7;
+  for (int j = 0; j < 9; ++j)
+    ptr9[((size_t)c * 9 + j) * kThreads + tid] = csr_ptr[(size_t)c * (kN * kN + 1) + y * kN + 8 * q + j];
+}
+
+size_t dft_smem_bytes(int A, int nnz) {
+  size_t b = 8 * (size_t)kSlab;            // F and the A/B operand slabs
+  b += 16 * (size_t)A + 16 * (size_t)A + 16 * (size_t)A;  // E, coefficients, self powers
+  b += 8 * (size_t)nnz;                     // gather entries
+  b += 16;                                  // mbarrier, TMEM address, abort flag
+  return b + 1024;                          // alignment slack
+}
+
+template <int XF>
+cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
+                       int* part_auto, cudaStream_t s) {
+  const int nnz = p.A * p.S * p.S;
+  dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef,
+                                                         p.d_ptr9, p.d_csr_ptr, p.d_csr_ent, nnz,
+                                                         reinterpret_cast<const uint4*>(p.d_fmat), part, part_auto,
+                                                         p.d_status);
+  return cudaGetLastError();
+}
+
+template <int XF>
+cudaError_t dft_attr(size_t smem) {
+  return cudaFuncSetAttribute(dft_image_kernel<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+bool dft_supported(int N, int P, int A, int S) {
+  if (N != kN || P != 2) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return dft_smem_bytes(A, A * S * S) <= (size_t)optin;
+}
+
+size_t dft_smem_need(int A, int S) { return dft_smem_bytes(A, A * S * S); }
+
+cudaError_t launch_dft_tables(Plan& p, cudaStream_t s) {
+  if (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_BF16)
+    dft_matrix_kernel<true><<<128, 128, 0, s>>>(p.d_fmat);
+  else
+    dft_matrix_kernel<false><<<128, 128, 0, s>>>(p.d_fmat);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ptr9_kernel<<<p.C, kThreads, 0, s>>>(p.C, p.d_csr_ptr, p.d_ptr9);
+  return cudaGetLastError();
+}
+
+cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
+  p.threads = kThreads;
+  p.smem = dft_smem_bytes(p.A, p.A * p.S * p.S);
+  p.ent_in_smem = 1;
+  cudaError_t e;
+  switch (p.xform) {
+    case EPIC_XFORM_DFT_BF16X3: e = dft_attr<EPIC_XFORM_DFT_BF16X3>(p.smem); break;
+    case EPIC_XFORM_DFT_FP16X3: e = dft_attr<EPIC_XFORM_DFT_FP16X3>(p.smem); break;
+    case EPIC_XFORM_DFT_BF16: e = dft_attr<EPIC_XFORM_DFT_BF16>(p.smem); break;
+    default: e = dft_attr<EPIC_XFORM_DFT_FP16>(p.smem); break;
+  }
+  if (e != cudaSuccess) return e;
+  *ctas_per_sm = 1;  // the kernel holds 256 TMEM columns and most of shared memory
+  return cudaSuccess;
+}
+
+cudaError_t launch_dft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
+                             int* part_auto, cudaStream_t s) {
+  switch (p.xform) {
+    case EPIC_XFORM_DFT_BF16X3: return dft_launch<EPIC_XFORM_DFT_BF16X3>(p, d_volts, T, ws, part, part_auto, s);
+    case EPIC_XFORM_DFT_FP16X3: return dft_launch<EPIC_XFORM_DFT_FP16X3>(p, d_volts, T, ws, part, part_auto, s);
+    case EPIC_XFORM_DFT_BF16: return dft_launch<EPIC_XFORM_DFT_BF16>(p, d_volts, T, ws, part, part_auto, s);
+    default: return dft_launch<EPIC_XFORM_DFT_FP16>(p, d_volts, T, ws, part, part_auto, s);
+  }
+}
+
+}  // namespace epic

@@ -45,6 +45,8 @@ struct Plan {
   int* d_csr_ptr = nullptr;     // [C][N*N+1] gather table: cell -> entries
   int2* d_csr_ent = nullptr;    // [C][A*S*S] (antenna, weight bits), antenna order
   float2* d_twiddle = nullptr;  // [N] exp(+2 pi i m / N)
+  uint16_t* d_fmat = nullptr;   // tensor path: real DFT matrix, hi/lo 16-bit, shared-memory image (64 KB)
+  int* d_ptr9 = nullptr;        // tensor path: [C][9][512] thread-major gather row pointers
   int* d_status = nullptr;      // device error word
 
   // imaging launch shape and its workspace (partial images per CTA span)
@@ -82,6 +84,14 @@ cudaError_t launch_twiddles(Plan& p, cudaStream_t s);
 cudaError_t fft_image_config(Plan& p, int* ctas_per_sm);
 cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws,
                              cudaStream_t s);
+
+// Tensor-core path (DFT-by-GEMM on tcgen05; N = 64, two polarisations).
+bool dft_supported(int N, int P, int A, int S);
+size_t dft_smem_need(int A, int S);
+cudaError_t launch_dft_tables(Plan& p, cudaStream_t s);
+cudaError_t dft_image_config(Plan& p, int* ctas_per_sm);
+cudaError_t launch_dft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
+                             int* part_auto, cudaStream_t s);
 
 // Block end: sum the CTA partials of every channel in a fixed order, remove the
 // autocorrelation term, write or accumulate the output.

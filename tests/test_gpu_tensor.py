@@ -1,0 +1,93 @@
+"""Parity of the tensor-core path (DFT-by-GEMM on tcgen05) with the FP64 oracle.
+
+The compensated transforms (BF16 or FP16 hi+lo, three products, FP32
+accumulation) must stay within 1e-3 of the channel's image peak; the plain
+16-bit transforms within the bounds stated below.  Errors are measured against
+the oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_1904_11422_gb300 import build_lib, epic, synth
+
+from _helpers import gpu_image, oracle_image, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+# stated bounds, relative to the channel's image peak (station-shaped data)
+TOL = {"dft_bf16x3": 1e-3, "dft_fp16x3": 1e-3, "dft_bf16": 2e-2, "dft_fp16": 5e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build_lib.build()
+    return epic.load_library()
+
+
+@pytest.fixture(scope="module")
+def station():
+    return synth.station()
+
+
+def test_small_array_bf16x3():
+    w = synth.random_small(901, n_ant=12, n_pol=2, n_chan=2, grid_n=64, support=3, n_time=3)
+    got = gpu_image(w, xform=epic.XFORMS["dft_bf16x3"])
+    ref = oracle_image(w)
+    err = rel_errors(got, ref, 2)
+    print("small bf16x3 errors", err.max())
+    assert err.max() <= TOL["dft_bf16x3"]
+
+
+@pytest.mark.parametrize("xf", ["dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+def test_random_arrays(xf):
+    for seed, kw in [(902, dict(n_ant=20, n_chan=3, support=5, n_time=11)),
+                     (903, dict(n_ant=40, n_chan=2, support=1, n_time=7))]:
+        w = synth.random_small(seed, n_pol=2, grid_n=64, **kw)
+        for sub in (True, False):
+            err = rel_errors(gpu_image(w, xform=epic.XFORMS[xf], subtract=sub), oracle_image(w, subtract=sub), 2)
+            assert err.max() <= TOL[xf], (xf, seed, sub, err.max())
+
+
+@pytest.mark.parametrize("xf", ["dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+def test_station_block_sampled_channels(station, xf):
+    w = station
+    got = gpu_image(w, xform=epic.XFORMS[xf])
+    chans = [0, 31, 63]
+    ref = oracle_image(w, channels=chans, use_fft=True)
+    err = rel_errors(got[chans], ref, 2)
+    print(f"{xf}: max error / image peak per plane {err.max(axis=0)}")
+    assert err.max() <= TOL[xf]
+
+
+def test_tensor_and_fp32_paths_agree_at_full_size(station):
+    w = station
+    a = gpu_image(w, xform=epic.XFORMS["dft_bf16x3"])
+    b = gpu_image(w, xform=epic.XFORMS["fft_fp32"])
+    assert rel_errors(a, b, 2).max() <= 1e-3
+
+
+def test_tensor_path_deterministic_and_additive(station):
+    import torch
+    w = station
+    plan = epic.plan_for(w, epic.XFORMS["dft_bf16x3"])
+    dv = torch.from_numpy(w.volts).cuda()
+    a = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    epic.epic_image(plan, dv, w.n_time, a, 0)
+    epic.epic_image(plan, dv, w.n_time, b, 0)
+    epic.epic_sync(plan)
+    assert torch.equal(a, b)
+    T1 = 600
+    epic.epic_image(plan, dv[:T1].contiguous(), T1, b, 0)
+    epic.epic_image(plan, dv[T1:].contiguous(), w.n_time - T1, b, 1)
+    epic.epic_sync(plan)
+    assert rel_errors(b.cpu().numpy(), a.cpu().numpy(), 2).max() < 1e-5
+    plan.close()
+
+
+def test_unsupported_shapes_are_rejected():
+    w = synth.random_small(904, n_ant=8, n_pol=1, n_chan=1, grid_n=64, support=3, n_time=2)
+    d, keep = epic.desc_from_workload(w, epic.XFORMS["dft_bf16x3"])
+    assert epic.epic_plan_validate(d) == epic.EPIC_ERR_UNSUPPORTED
+    w = synth.random_small(905, n_ant=8, n_pol=2, n_chan=1, grid_n=32, support=3, n_time=2)
+    d, keep = epic.desc_from_workload(w, epic.XFORMS["dft_bf16x3"])
+    assert epic.epic_plan_validate(d) == epic.EPIC_ERR_UNSUPPORTED
