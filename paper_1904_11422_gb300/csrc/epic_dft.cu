@@ -4,18 +4,25 @@
 //
 // With F[k][x] = exp(+2 pi i (k - N/2) x / N) (the pixel shift of reading R4
 // folded into the rows), one (t, c) image set is Y_g = F G_g F^T for the two
-// polarisation grids g.  Each complex product is one real GEMM on the 2N x 2N
-// matrix [[Fr, -Fi], [Fi, Fr]] (rows interleaved re/im):
-//   stage 1 (along x): D1[(g,y)][(k,c)]  = sum_(c',x) G[(g,y)][(c',x)] Fre[(k,c)][(c',x)]
-//   stage 2 (along y): D2[(j,c)][(g,k)]  = sum_(c',y) Fre[(j,c)][(c',y)] Z[(g,k)][(c',y)]
-// with Z the stage-1 result moved from TMEM to shared memory.  At N = 64 both are
-// M = N = K = 128 GEMMs, A and B K-major in 128-byte-swizzled shared memory, the
-// FP32 accumulators in tensor memory.  The operands are split into a high and a
-// low 16-bit part (BF16 or FP16) and three products hi.hi + hi.lo + lo.hi are
-// accumulated (the "x3" transforms), or only the high parts are used.
+// polarisation grids g.  Each complex product is one real GEMM with the 2N x 2N
+// matrix Fre = [[Fr, -Fi], [Fi, Fr]] (rows interleaved re/im) as the A operand:
+//   stage 1 (along x): D1[(k,c)][(g,y)] = sum_(c',x) Fre[(k,c)][(c',x)] G[(g,y)][(c',x)]
+//   stage 2 (along y): D2[(j,c)][(g,k)] = sum_(c',y) Fre[(j,c)][(c',y)] Z[(g,k)][(c',y)]
+// where Z[(g,k)][(c,y)] = D1[(k,c)][(g,y)] is moved from tensor memory to shared
+// memory (each thread holds 32 consecutive y of one row, so the transposition
+// costs only 16-byte stores).  At N = 64 both stages are M = N = K = 128 GEMMs:
+// Fre lives in tensor memory for the whole launch (A operand), the gridded
+// fields and Z are K-major 128-byte-swizzled shared-memory B operands, and the
+// FP32 accumulators are in tensor memory.  The operands are split into a high
+// and a low 16-bit part (BF16 or FP16) and three products hi.hi + lo.hi + hi.lo
+// are accumulated (the "x3" transforms), or only the high parts are used.
 //
-// One elected thread issues the MMAs and commits them to an mbarrier; every wait
-// on it is bounded (about one second) and reports EPIC_ERR_TIMEOUT through the
+// The samples of a CTA are software-pipelined: the stage-2 products of sample t
+// run while sample t+1 is unpacked and gridded, and the stage-1 products of t+1
+// run while sample t is squared and accumulated.
+//
+// One elected thread issues the MMAs and commits them to mbarriers; every wait
+// on them is bounded (about one second) and reports EPIC_ERR_TIMEOUT through the
 // plan's status word instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -28,7 +35,6 @@ namespace {
 
 constexpr int kN = 64;               // grid side of this kernel
 constexpr int kThreads = 512;        // 16 warps
-constexpr int kTmemCols = 256;       // D1 at columns [0,128), D2 at [128,256)
 constexpr int kSlab = 128 * 128;     // one 128-row x 64-element 16-bit operand slab, bytes
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bounded waits: one second
 
@@ -76,14 +82,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   while (!mbar_try_wait(bar, parity))
     if (global_ns() - t0 > kWaitNs) return false;
   return true;
-}
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -157,24 +155,68 @@ __device__ __forceinline__ float from16(unsigned short h) {
   else return __half2float(__ushort_as_half(h));
 }
 
-// Shared memory of the kernel (offsets from a 1024-byte aligned base).
+// 16 consecutive 32-bit TMEM columns written from the warp's 32 lanes.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// MMA with the A operand read from tensor memory (K-major rows in TMEM lanes,
+// two 16-bit K elements per 32-bit column) and B from shared memory.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Two floats to a packed pair of 16-bit values (low half = first) and back.
+template <bool kBf16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (kBf16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+template <bool kBf16>
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+  if constexpr (kBf16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+  else return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+
+// TMEM columns (512 allocated): the DFT matrix as A operand (hi, lo), the
+// stage-1 accumulator D1 and two stage-2 accumulators D2 (double-buffered so the
+// squaring of one sample overlaps the stage-2 products of the next).
+constexpr uint32_t kColFhi = 0, kColFlo = 64, kColD1 = 128, kColD2 = 256;
+
+// Shared memory (offsets from a 1024-byte aligned base).
 struct DftSmem {
-  static constexpr uint32_t F = 0;                // 4 slabs: hi K0-63, hi K64-127, lo K0-63, lo K64-127
-  static constexpr uint32_t AB = 4 * kSlab;       // 4 slabs: the gridded fields (stage-1 A), then Z (stage-2 B)
-  static constexpr uint32_t E = 8 * kSlab;        // [A] float4 calibrated fields
+  static constexpr uint32_t B1 = 0;          // gridded fields, rows (g, y), K = (c', x): hi re, hi im, lo re, lo im
+  static constexpr uint32_t B2 = 4 * kSlab;  // stage-1 result, rows (g, k), K = (c', y): same four slabs
+  static constexpr uint32_t E = 8 * kSlab;   // [A] float4 calibrated fields, then coefficients, self powers, entries
 };
 
 template <int XF>
 __global__ void __launch_bounds__(kThreads, 1)
     dft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
-                     const float2* __restrict__ coef, const int* __restrict__ ptr9, const int* __restrict__ csr_ptr,
-                     const int2* __restrict__ csr_ent, int nnz, const uint4* __restrict__ fmat,
-                     float* __restrict__ part, int* __restrict__ part_auto, int* __restrict__ status) {
+                     const float2* __restrict__ coef, const int* __restrict__ ptr9, const int2* __restrict__ csr_ent,
+                     int nnz, const uint32_t* __restrict__ fmat, float* __restrict__ part,
+                     int* __restrict__ part_auto, int* __restrict__ status) {
   using Pr = Prec<XF>;
+  constexpr bool kBf = Pr::kBf16;
   constexpr int NN = kN * kN;
-  constexpr uint32_t kIdesc = idesc_m128n128<Pr::kBf16>();
+  constexpr uint32_t kIdesc = idesc_m128n128<kBf>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // 1024-byte alignment for the swizzle atoms
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char* sm = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(sm);
@@ -182,8 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float2* coef_s = reinterpret_cast<float2*>(E4 + A);       // [A][2]
   int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A);    // [A]
   int2* ent_s = reinterpret_cast<int2*>(auto_s + A);         // [nnz]
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(ent_s + nnz);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ent_s + nnz);  // stage 1, stage 2
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -191,34 +233,49 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long u1 = min(u0 + W, units);
   if (u0 >= u1) return;
   const int c_first = (int)(u0 / T);
+  const uint32_t bar1 = smem_u32(&bars[0]), bar2 = smem_u32(&bars[1]);
 
-  // ---- one-time set-up: TMEM, mbarrier, the DFT matrix in shared memory ----
+  // ---- set-up: TMEM, mbarriers, the DFT matrix into TMEM ----
   if (warp == 0) {
-    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    tmem_alloc(smem_u32(tmem_slot), 512);
     tmem_relinquish();
     tc_fence_before();
   }
   if (tid == 0) {
-    mbar_init(smem_u32(bar), 1);
+    mbar_init(bar1, 1);
+    mbar_init(bar2, 1);
     fence_mbar_init();
     *abort_flag = 0;
   }
-  {
-    uint4* dstF = reinterpret_cast<uint4*>(sm + DftSmem::F);
-    for (int k = tid; k < 4 * kSlab / 16; k += kThreads) dstF[k] = fmat[k];
-  }
-  fence_proxy_async();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tmem_d1 = tmem, tmem_d2 = tmem + 128;
-  uint32_t phase = 0, pending = 0;
+  const int lg = warp & 3, cq = warp >> 2;  // TMEM lane group, column quarter
+  const uint32_t lane_base = (uint32_t)(32 * lg) << 16;
+  if (warp < 4) {
+    // row m = 32 lg + lane of the real DFT matrix, hi then lo, 64 packed columns each
+    const uint32_t* src = fmat + (size_t)(32 * lg + lane) * 64;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t r[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = src[(size_t)h * 128 * 64 + 16 * q + j];
+        tmem_st16(tmem + lane_base + (h ? kColFlo : kColFhi) + 16 * q, r);
+      }
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
-  // thread roles for the CUDA-core phases
-  const int gy = tid >> 3, gq = tid & 7;                  // gridder: row y, cells x = 8q..8q+7
-  const int lg = warp & 3, cq = warp >> 2;                // TMEM lane group, column quarter
-  // epilogue: lanes (j, c) = (16*lg + lane/2, lane&1); columns k in [16 cq, 16 cq + 16) of both grids
-  const int ej = 16 * lg + (lane >> 1), ec = lane & 1;
+  uint32_t ph1 = 0, ph2 = 0, pend1 = 0, pend2 = 0;
+  int d2buf = 0, have_prev = 0, prev_buf = 0;
+  const int gy = tid >> 3, gq = tid & 7;                 // gridder: row y, cells x = 8q..8q+7
+  const int ej = 16 * lg + (lane >> 1), ec = lane & 1;   // epilogue lanes (j, c) of D2
+  const int ck = 16 * lg + (lane >> 1), cc = lane & 1;   // conversion lanes (k, c) of D1
+  const int cg = cq >> 1, cy0 = 32 * (cq & 1);           // conversion columns (g, y0 .. y0+31)
 
   float acc[4][8];
 #pragma unroll
@@ -226,8 +283,37 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
 
-  int cur_c = -1;
-  int p9[9];
+  auto wait_or_abort = [&](uint32_t bar, uint32_t& ph, uint32_t& pend) {
+    if (!mbar_wait_bounded(bar, ph)) {
+      atomicExch(status, kDevTimeout);
+      *abort_flag = 1;
+    }
+    pend = ph;
+    ph ^= 1;
+    tc_fence_after();
+  };
+
+  // squaring and accumulation of one stage-2 result (TMEM lanes (j, c), columns
+  // (g, k)); partner lanes 2j / 2j+1 exchange the other component
+  auto epilogue = [&](int buf) {
+    float X[16], Y[16];
+    const uint32_t d2 = tmem + lane_base + kColD2 + 128 * buf;
+    tmem_ld16(d2 + 16 * cq, X);
+    tmem_ld16(d2 + 64 + 16 * cq, Y);
+    tmem_wait_ld();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float sx = ec ? X[s] : X[8 + s], sy = ec ? Y[s] : Y[8 + s];
+      const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
+      const float xr = ec ? rx : X[s], xi = ec ? X[8 + s] : rx;
+      const float yr = ec ? ry : Y[s], yi = ec ? Y[8 + s] : ry;
+      acc[0][s] = fmaf(xr, xr, fmaf(xi, xi, acc[0][s]));
+      acc[1][s] = fmaf(yr, yr, fmaf(yi, yi, acc[1][s]));
+      acc[2][s] = fmaf(xr, yr, fmaf(xi, yi, acc[2][s]));
+      acc[3][s] = fmaf(xi, yr, fmaf(-xr, yi, acc[3][s]));
+    }
+  };
+
   auto flush = [&](int c) {
     const int slot = c - c_first;
     float* dst = part + (size_t)((long long)blockIdx.x * spans + slot) * 4 * NN;
@@ -241,9 +327,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int a = tid; a < A; a += kThreads) pa[a] = auto_s[a];
   };
 
+  int cur_c = -1;
+  int p9[9];
   for (long long u = u0; u < u1; ++u) {
     const int c = (int)(u / T), t = (int)(u % T);
     if (c != cur_c) {
+      if (have_prev) {  // the last sample of the previous channel still owes its squares
+        wait_or_abort(bar2, ph2, pend2);
+        epilogue(prev_buf);
+        have_prev = 0;
+      }
       if (cur_c >= 0) {
         flush(cur_c);
 #pragma unroll
@@ -252,6 +345,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
       }
       cur_c = c;
+      tc_fence_before();
+      __syncthreads();
       for (int k = tid; k < 2 * A; k += kThreads) coef_s[k] = coef[(size_t)c * A * 2 + k];
       for (int a = tid; a < A; a += kThreads) auto_s[a] = make_int4(0, 0, 0, 0);
       const int2* src = csr_ent + (size_t)c * nnz;
@@ -281,8 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
-    // 2. grid 8 cells (y, 8q..8q+7) of both polarisations and store them, split
-    //    into 16-bit hi/lo parts, as rows (g, y) of the stage-1 A operand
+    // 2. grid cells (y, 8q..8q+7) of both polarisations into rows (g, y) of the
+    //    stage-1 B operand, split into 16-bit hi/lo parts (the previous sample's
+    //    stage-1 products, which read this buffer, completed before its conversion)
     {
       float gre[2][8], gim[2][8];
 #pragma unroll
@@ -301,25 +397,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
-        const int row = g * kN + gy;
-        const uint32_t off = slab_off(row, 8 * gq);
+        const uint32_t off = slab_off(g * kN + gy, 8 * gq);
 #pragma unroll
         for (int comp = 0; comp < 2; ++comp) {
           const float* v = comp ? gim[g] : gre[g];
           uint32_t hi[4], lo[4];
 #pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const unsigned short h0 = to16<Pr::kBf16>(v[2 * s]), h1 = to16<Pr::kBf16>(v[2 * s + 1]);
-            hi[s] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+          for (int q = 0; q < 4; ++q) {
+            hi[q] = pack2<kBf>(v[2 * q], v[2 * q + 1]);
             if constexpr (Pr::kSplit) {
-              const unsigned short l0 = to16<Pr::kBf16>(v[2 * s] - from16<Pr::kBf16>(h0));
-              const unsigned short l1 = to16<Pr::kBf16>(v[2 * s + 1] - from16<Pr::kBf16>(h1));
-              lo[s] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+              const float2 back = unpack2<kBf>(hi[q]);
+              lo[q] = pack2<kBf>(v[2 * q] - back.x, v[2 * q + 1] - back.y);
             }
           }
-          *reinterpret_cast<uint4*>(sm + DftSmem::AB + comp * kSlab + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(sm + DftSmem::B1 + comp * kSlab + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
           if constexpr (Pr::kSplit)
-            *reinterpret_cast<uint4*>(sm + DftSmem::AB + (2 + comp) * kSlab + off) =
+            *reinterpret_cast<uint4*>(sm + DftSmem::B1 + (2 + comp) * kSlab + off) =
                 make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
@@ -327,130 +420,113 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_proxy_async();
     __syncthreads();
 
-    // 3. stage 1: D1 = A1 . Fre^T (3 or 1 products, K = 128 in steps of 16)
+    // 3. stage 1: D1 = Fre . G^T, lanes (k, c), columns (g, y)
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t aHi = sbase + DftSmem::AB, aLo = aHi + 2 * kSlab;
-      const uint32_t fHi = sbase + DftSmem::F, fLo = fHi + 2 * kSlab;
+      const uint32_t gHi = sbase + DftSmem::B1, gLo = gHi + 2 * kSlab;
       uint32_t accum = 0;
 #pragma unroll
       for (int pr = 0; pr < (Pr::kSplit ? 3 : 1); ++pr) {
-        const uint32_t a = (pr == 2) ? aLo : aHi;
-        const uint32_t b = (pr == 1) ? fLo : fHi;
+        const uint32_t fcol = (pr == 1) ? kColFlo : kColFhi;
+        const uint32_t b = (pr == 2) ? gLo : gHi;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-          const uint32_t koff = (kk >> 2) * kSlab + (kk & 3) * 32;
-          mma_f16(tmem_d1, sdesc_sw128(a + koff), sdesc_sw128(b + koff), kIdesc, accum);
+          mma_f16_ts(tmem + kColD1, tmem + fcol + 8 * kk, sdesc_sw128(b + (kk >> 2) * kSlab + (kk & 3) * 32),
+                     kIdesc, accum);
           accum = 1;
         }
       }
-      mma_commit(smem_u32(bar));
+      mma_commit(bar1);
     }
-    if (!mbar_wait_bounded(smem_u32(bar), phase)) {
-      atomicExch(status, kDevTimeout);
-      *abort_flag = 1;
-    }
-    pending = phase;
-    phase ^= 1;
-    tc_fence_after();
 
-    // 4. Z = D1 (TMEM lanes (g, y), columns (k, c)) -> stage-2 B operand rows
-    //    (g, k), K = (c, y), split hi/lo; warp covers lanes 32 lg.., k in [16 cq, +16)
+    // 4. while stage 1 runs: squares of the previous sample
+    if (have_prev) {
+      wait_or_abort(bar2, ph2, pend2);
+      epilogue(prev_buf);
+    }
+
+    // 5. Z = D1 -> stage-2 B operand rows (g, k), K = (c, y), split hi/lo; the
+    //    previous sample's stage-2 products, which read this buffer, are complete
+    wait_or_abort(bar1, ph1, pend1);
     {
-      const int g = lg >> 1, y = 32 * (lg & 1) + lane;
-      float v[2][16];
-      tmem_ld16(tmem_d1 + ((uint32_t)(32 * lg) << 16) + 32 * cq, v[0]);
-      tmem_ld16(tmem_d1 + ((uint32_t)(32 * lg) << 16) + 32 * cq + 16, v[1]);
+      float v[32];
+      const uint32_t d1 = tmem + lane_base + kColD1 + 32 * cq;
+      tmem_ld16(d1, *reinterpret_cast<float(*)[16]>(&v[0]));
+      tmem_ld16(d1 + 16, *reinterpret_cast<float(*)[16]>(&v[16]));
       tmem_wait_ld();
+      const int row = cg * kN + ck;
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int q = 0; q < 4; ++q) {
+        uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int k = 16 * cq + 8 * h + s;
-          const int row = g * kN + k;
-#pragma unroll
-          for (int comp = 0; comp < 2; ++comp) {
-            const float val = v[h][2 * s + comp];
-            const unsigned short hi = to16<Pr::kBf16>(val);
-            const uint32_t off = slab_off(row, y);
-            *reinterpret_cast<unsigned short*>(sm + DftSmem::AB + comp * kSlab + off) = hi;
-            if constexpr (Pr::kSplit)
-              *reinterpret_cast<unsigned short*>(sm + DftSmem::AB + (2 + comp) * kSlab + off) =
-                  to16<Pr::kBf16>(val - from16<Pr::kBf16>(hi));
+        for (int h = 0; h < 4; ++h) {
+          hi[h] = pack2<kBf>(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+          if constexpr (Pr::kSplit) {
+            const float2 back = unpack2<kBf>(hi[h]);
+            lo[h] = pack2<kBf>(v[8 * q + 2 * h] - back.x, v[8 * q + 2 * h + 1] - back.y);
           }
         }
+        const uint32_t off = slab_off(row, cy0 + 8 * q);
+        *reinterpret_cast<uint4*>(sm + DftSmem::B2 + cc * kSlab + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if constexpr (Pr::kSplit)
+          *reinterpret_cast<uint4*>(sm + DftSmem::B2 + (2 + cc) * kSlab + off) =
+              make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
     }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     if (*abort_flag) break;
 
-    // 5. stage 2: D2 = Fre . Z^T
+    // 6. stage 2: D2[buf] = Fre . Z^T, lanes (j, c), columns (g, k); runs while
+    //    the next sample is unpacked and gridded
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t zHi = sbase + DftSmem::AB, zLo = zHi + 2 * kSlab;
-      const uint32_t fHi = sbase + DftSmem::F, fLo = fHi + 2 * kSlab;
+      const uint32_t zHi = sbase + DftSmem::B2, zLo = zHi + 2 * kSlab;
       uint32_t accum = 0;
 #pragma unroll
       for (int pr = 0; pr < (Pr::kSplit ? 3 : 1); ++pr) {
-        const uint32_t a = (pr == 2) ? fLo : fHi;
-        const uint32_t b = (pr == 1) ? zLo : zHi;
+        const uint32_t fcol = (pr == 1) ? kColFlo : kColFhi;
+        const uint32_t b = (pr == 2) ? zLo : zHi;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-          const uint32_t koff = (kk >> 2) * kSlab + (kk & 3) * 32;
-          mma_f16(tmem_d2, sdesc_sw128(a + koff), sdesc_sw128(b + koff), kIdesc, accum);
+          mma_f16_ts(tmem + kColD2 + 128 * d2buf, tmem + fcol + 8 * kk,
+                     sdesc_sw128(b + (kk >> 2) * kSlab + (kk & 3) * 32), kIdesc, accum);
           accum = 1;
         }
       }
-      mma_commit(smem_u32(bar));
+      mma_commit(bar2);
     }
-    if (!mbar_wait_bounded(smem_u32(bar), phase)) {
-      atomicExch(status, kDevTimeout);
-      *abort_flag = 1;
-    }
-    pending = phase;
-    phase ^= 1;
-    tc_fence_after();
-
-    // 6. products: D2 lanes (j, c), columns (g, k); pair lanes 2j / 2j+1 exchange
-    //    the other component, each keeps 8 of the warp's 16 columns
-    {
-      float X[16], Y[16];
-      tmem_ld16(tmem_d2 + ((uint32_t)(32 * lg) << 16) + 16 * cq, X);
-      tmem_ld16(tmem_d2 + ((uint32_t)(32 * lg) << 16) + 64 + 16 * cq, Y);
-      tmem_wait_ld();
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        // lane c = 0 keeps k = s (sends its real parts of k = 8 + s); c = 1 keeps k = 8 + s
-        const float sx = ec ? X[s] : X[8 + s], sy = ec ? Y[s] : Y[8 + s];
-        const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
-        const float xr = ec ? rx : X[s], xi = ec ? X[8 + s] : rx;
-        const float yr = ec ? ry : Y[s], yi = ec ? Y[8 + s] : ry;
-        acc[0][s] = fmaf(xr, xr, fmaf(xi, xi, acc[0][s]));
-        acc[1][s] = fmaf(yr, yr, fmaf(yi, yi, acc[1][s]));
-        acc[2][s] = fmaf(xr, yr, fmaf(xi, yi, acc[2][s]));
-        acc[3][s] = fmaf(xi, yr, fmaf(-xr, yi, acc[3][s]));
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_flag) break;
+    have_prev = 1;
+    prev_buf = d2buf;
+    d2buf ^= 1;
   }
-  if (cur_c >= 0 && !*abort_flag) flush(cur_c);
-  // after a timed-out wait the MMAs may still be running: give them one more
-  // bounded wait before the tensor memory they write is released
-  if (*abort_flag) mbar_wait_bounded(smem_u32(bar), pending);
+  if (!*abort_flag) {
+    if (have_prev) {
+      wait_or_abort(bar2, ph2, pend2);
+      epilogue(prev_buf);
+    }
+    if (cur_c >= 0) flush(cur_c);
+  }
+  // after a timed-out wait the MMAs may still be running: one more bounded wait
+  // on each barrier before the tensor memory they write is released
+  if (*abort_flag) {
+    mbar_wait_bounded(bar1, pend1);
+    mbar_wait_bounded(bar2, pend2);
+  }
+  tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, kTmemCols);
+    tmem_dealloc(tmem, 512);
   }
 }
 
 // ---- plan-time tables ----------------------------------------------------------
-// The real 2N x 2N DFT matrix, rows m = 2k + c (c = 0 real, 1 imaginary output
-// part), columns K = c' N + x, split hi/lo in FP64 and written as the byte image
-// of the four shared-memory slabs the kernel copies.
+// The real 2N x 2N DFT matrix [[Fr, -Fi], [Fi, Fr]] with rows m = 2k + c (c = 0
+// real, 1 imaginary output part) and columns K = c' N + x, split into 16-bit hi
+// and lo parts in FP64, stored row-major as packed pairs (element K in the low
+// half of word K/2 when K is even): [2 (hi, lo)][128 rows][64 words].
 template <bool kBf16>
 __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
   const int m = blockIdx.x;          // 0..127
@@ -460,7 +536,7 @@ __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
   const int ph = (((f * x) % kN) + kN) % kN;
   double sn, cs;
   sincospi(2.0 * (double)ph / (double)kN, &sn, &cs);
-  // [[Fr, -Fi], [Fi, Fr]]: output re = Fr*Gr - Fi*Gi ; output im = Fi*Gr + Fr*Gi
+  // output re = Fr Gr - Fi Gi ; output im = Fi Gr + Fr Gi
   const double v = (c == 0) ? (cp == 0 ? cs : -sn) : (cp == 0 ? sn : cs);
   uint16_t hi, lo;
   if (kBf16) {
@@ -472,9 +548,8 @@ __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
     hi = __half_as_ushort(h);
     lo = __half_as_ushort(__double2half(v - (double)__half2float(h)));
   }
-  const uint32_t off = slab_off(m, x) / 2;
-  out[(size_t)(0 * 2 + cp) * (kSlab / 2) + off] = hi;
-  out[(size_t)(1 * 2 + cp) * (kSlab / 2) + off] = lo;
+  out[(size_t)m * 128 + kk] = hi;
+  out[(size_t)128 * 128 + (size_t)m * 128 + kk] = lo;
 }
 
 // Thread-major row pointers of the gridder: thread (y, q) owns cells
@@ -487,10 +562,10 @@ __global__ void ptr9_kernel(int C, const int* __restrict__ csr_ptr, int* __restr
 }
 
 size_t dft_smem_bytes(int A, int nnz) {
-  size_t b = 8 * (size_t)kSlab;            // F and the A/B operand slabs
+  size_t b = 8 * (size_t)kSlab;            // the two B operands (gridded fields, stage-1 result)
   b += 16 * (size_t)A + 16 * (size_t)A + 16 * (size_t)A;  // E, coefficients, self powers
   b += 8 * (size_t)nnz;                     // gather entries
-  b += 16;                                  // mbarrier, TMEM address, abort flag
+  b += 32;                                  // two mbarriers, TMEM address, abort flag
   return b + 1024;                          // alignment slack
 }
 
@@ -499,9 +574,9 @@ cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkS
                        int* part_auto, cudaStream_t s) {
   const int nnz = p.A * p.S * p.S;
   dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef,
-                                                         p.d_ptr9, p.d_csr_ptr, p.d_csr_ent, nnz,
-                                                         reinterpret_cast<const uint4*>(p.d_fmat), part, part_auto,
-                                                         p.d_status);
+                                                         p.d_ptr9, p.d_csr_ent, nnz,
+                                                         reinterpret_cast<const uint32_t*>(p.d_fmat), part,
+                                                         part_auto, p.d_status);
   return cudaGetLastError();
 }
 
@@ -545,7 +620,7 @@ cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
     default: e = dft_attr<EPIC_XFORM_DFT_FP16>(p.smem); break;
   }
   if (e != cudaSuccess) return e;
-  *ctas_per_sm = 1;  // the kernel holds 256 TMEM columns and most of shared memory
+  *ctas_per_sm = 1;  // the kernel holds all 512 TMEM columns
   return cudaSuccess;
 }
 
