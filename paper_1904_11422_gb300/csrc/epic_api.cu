@@ -28,8 +28,10 @@ constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA on sm_100
 
 bool grid_supported(int xform, int N, int P, int A, int S) {
   if (xform == EPIC_XFORM_FFT_FP32) return (N == 32 || N == 64) && A <= kMaxAntFft;
-  // tensor path: 64 x 64 grids of two polarisations, gather table in shared memory
-  return N == 64 && P == 2 && epic::dft_smem_need(A, S) <= kSmemOptin;
+  // tensor path: 64 x 64 grids of two polarisations, with the gather entries in
+  // shared memory (bounded here by the unpadded count A S^2; the exact padded
+  // count is checked when the plan is created)
+  return N == 64 && P == 2 && epic::dft_smem_need(A, A * S * S) <= kSmemOptin;
 }
 
 epic_status from_cuda(cudaError_t e) {
@@ -58,9 +60,10 @@ void free_plan(Plan& p) {
   p.event_pool.clear();
   void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
                   p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
-                  p.d_stage_in, p.d_stage_out, p.d_fmat, p.d_ptr9};
+                  p.d_stage_in, p.d_stage_out, p.d_fmat};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  epic::free_gather_tables(p.gt);
 }
 
 // Work units u = c*T + t (channel-major) split into equal contiguous ranges,
@@ -258,11 +261,21 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   }
 
   int per_sm = 0;
+  size_t gt_bytes = 0;
   if (p.xform == EPIC_XFORM_FFT_FP32) {
+    EPIC_TRY(epic::build_gather_tables(p, p.N == 64 ? epic::kLayoutFft64 : epic::kLayoutFft32,
+                                       p.N == 64 ? 512 : 128, 0, &gt_bytes));
+    total += gt_bytes;
     EPIC_TRY(epic::fft_image_config(p, &per_sm));
   } else {
+    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutChunk64, 512, 1, &gt_bytes));
+    total += gt_bytes;
+    if (epic::dft_smem_need(p.A, p.gt.max_chan_entries) > kSmemOptin) {
+      free_plan(p);
+      delete h;
+      return EPIC_ERR_UNSUPPORTED;  // the padded gather table does not fit in shared memory
+    }
     EPIC_TRY(alloc(&p.d_fmat, (size_t)4 * 128 * 128 / 2, &total));
-    EPIC_TRY(alloc(&p.d_ptr9, C * 9 * 512, &total));
     EPIC_TRY(epic::launch_dft_tables(p, 0));
     EPIC_TRY(cudaDeviceSynchronize());
     EPIC_TRY(epic::dft_image_config(p, &per_sm));

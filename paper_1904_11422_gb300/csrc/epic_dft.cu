@@ -209,9 +209,11 @@ struct DftSmem {
 template <int XF>
 __global__ void __launch_bounds__(kThreads, 1)
     dft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
-                     const float2* __restrict__ coef, const int* __restrict__ ptr9, const int2* __restrict__ csr_ent,
-                     int nnz, const uint32_t* __restrict__ fmat, float* __restrict__ part,
-                     int* __restrict__ part_auto, int* __restrict__ status) {
+                     const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
+                     const int* __restrict__ g_off, const uint16_t* __restrict__ g_task,
+                     const uint16_t* __restrict__ g_ent_a, const float* __restrict__ g_ent_w, int max_entries,
+                     const uint32_t* __restrict__ fmat, float* __restrict__ part, int* __restrict__ part_auto,
+                     int* __restrict__ status) {
   using Pr = Prec<XF>;
   constexpr bool kBf = Pr::kBf16;
   constexpr int NN = kN * kN;
@@ -223,10 +225,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   float4* E4 = reinterpret_cast<float4*>(sm + DftSmem::E);
   float2* coef_s = reinterpret_cast<float2*>(E4 + A);       // [A][2]
   int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A);    // [A]
-  int2* ent_s = reinterpret_cast<int2*>(auto_s + A);         // [nnz]
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ent_s + nnz);  // stage 1, stage 2
+  int* cnt_s = reinterpret_cast<int*>(auto_s + A);           // [16 warps][8] trip counts
+  int* base_s = cnt_s + 16 * 8;                              // [16 warps][8] first entries
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base_s + 16 * 8);  // stage 1, stage 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  float* entw_s = reinterpret_cast<float*>(abort_flag + 3);  // [max_entries]
+  uint16_t* enta_s = reinterpret_cast<uint16_t*>(entw_s + max_entries);  // [max_entries]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long u0 = (long long)blockIdx.x * W;
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint32_t ph1 = 0, ph2 = 0, pend1 = 0, pend2 = 0;
   int d2buf = 0, have_prev = 0, prev_buf = 0;
-  const int gy = tid >> 3, gq = tid & 7;                 // gridder: row y, cells x = 8q..8q+7
+  int gy = 0, gq = 0;                                    // gridder task: row y, cells x = 8q..8q+7
   const int ej = 16 * lg + (lane >> 1), ec = lane & 1;   // epilogue lanes (j, c) of D2
   const int ck = 16 * lg + (lane >> 1), cc = lane & 1;   // conversion lanes (k, c) of D1
   const int cg = cq >> 1, cy0 = 32 * (cq & 1);           // conversion columns (g, y0 .. y0+31)
@@ -328,7 +333,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
 
   int cur_c = -1;
-  int p9[9];
   for (long long u = u0; u < u1; ++u) {
     const int c = (int)(u / T), t = (int)(u % T);
     if (c != cur_c) {
@@ -349,10 +353,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
       for (int k = tid; k < 2 * A; k += kThreads) coef_s[k] = coef[(size_t)c * A * 2 + k];
       for (int a = tid; a < A; a += kThreads) auto_s[a] = make_int4(0, 0, 0, 0);
-      const int2* src = csr_ent + (size_t)c * nnz;
-      for (int k = tid; k < nnz; k += kThreads) ent_s[k] = src[k];
-#pragma unroll
-      for (int j = 0; j < 9; ++j) p9[j] = ptr9[((size_t)c * 9 + j) * kThreads + tid];
+      if (tid < 16 * 8) {
+        cnt_s[tid] = g_cnt[(size_t)c * 16 * 8 + tid];
+        base_s[tid] = g_base[(size_t)c * 16 * 8 + tid];
+      }
+      const int e0 = g_off[c], ne = g_off[c + 1] - e0;
+      for (int k = tid; k < ne; k += kThreads) {
+        enta_s[k] = g_ent_a[e0 + k];
+        entw_s[k] = g_ent_w[e0 + k];
+      }
+      const int task = g_task[(size_t)c * kThreads + tid];
+      gy = task >> 3;
+      gq = task & 7;
       __syncthreads();
     }
 
@@ -383,11 +395,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       float gre[2][8], gim[2][8];
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
+        // lane-interleaved entries of cell (y, 8q + s), warp-uniform trip count
+        const int K = cnt_s[warp * 8 + s];
+        const int b = base_s[warp * 8 + s] + lane;
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
-        for (int e = p9[s]; e < p9[s + 1]; ++e) {
-          const int2 en = ent_s[e];
-          const float w = __int_as_float(en.y);
-          const float4 ev = E4[en.x];
+        for (int k = 0; k < K; ++k) {
+          const float w = entw_s[b + 32 * k];
+          const float4 ev = E4[enta_s[b + 32 * k]];
           xr = fmaf(w, ev.x, xr);
           xi = fmaf(w, ev.y, xi);
           yr = fmaf(w, ev.z, yr);
@@ -552,31 +566,22 @@ __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
   out[(size_t)128 * 128 + (size_t)m * 128 + kk] = lo;
 }
 
-// Thread-major row pointers of the gridder: thread (y, q) owns cells
-// (y, 8q .. 8q+7); entry j of its list is the CSR pointer of cell 8q + j.
-__global__ void ptr9_kernel(int C, const int* __restrict__ csr_ptr, int* __restrict__ ptr9) {
-  const int c = blockIdx.x, tid = threadIdx.x;
-  const int y = tid >> 3, q = tid & 7;
-  for (int j = 0; j < 9; ++j)
-    ptr9[((size_t)c * 9 + j) * kThreads + tid] = csr_ptr[(size_t)c * (kN * kN + 1) + y * kN + 8 * q + j];
-}
-
-size_t dft_smem_bytes(int A, int nnz) {
+size_t dft_smem_bytes(int A, int max_entries) {
   size_t b = 8 * (size_t)kSlab;            // the two B operands (gridded fields, stage-1 result)
   b += 16 * (size_t)A + 16 * (size_t)A + 16 * (size_t)A;  // E, coefficients, self powers
-  b += 8 * (size_t)nnz;                     // gather entries
+  b += 2 * 16 * 8 * sizeof(int);            // gather trip counts and bases
   b += 32;                                  // two mbarriers, TMEM address, abort flag
+  b += 6 * (size_t)max_entries;             // gather entries (weight, antenna)
   return b + 1024;                          // alignment slack
 }
 
 template <int XF>
 cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                        int* part_auto, cudaStream_t s) {
-  const int nnz = p.A * p.S * p.S;
-  dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef,
-                                                         p.d_ptr9, p.d_csr_ent, nnz,
-                                                         reinterpret_cast<const uint32_t*>(p.d_fmat), part,
-                                                         part_auto, p.d_status);
+  dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(
+      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+      p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, reinterpret_cast<const uint32_t*>(p.d_fmat),
+      part, part_auto, p.d_status);
   return cudaGetLastError();
 }
 
@@ -587,30 +592,21 @@ cudaError_t dft_attr(size_t smem) {
 
 }  // namespace
 
-bool dft_supported(int N, int P, int A, int S) {
-  if (N != kN || P != 2) return false;
-  int dev = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return dft_smem_bytes(A, A * S * S) <= (size_t)optin;
-}
-
-size_t dft_smem_need(int A, int S) { return dft_smem_bytes(A, A * S * S); }
+// Shared memory the tensor kernel needs for a plan whose largest channel has
+// max_entries padded gather entries.
+size_t dft_smem_need(int A, int max_entries) { return dft_smem_bytes(A, max_entries); }
 
 cudaError_t launch_dft_tables(Plan& p, cudaStream_t s) {
   if (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_BF16)
     dft_matrix_kernel<true><<<128, 128, 0, s>>>(p.d_fmat);
   else
     dft_matrix_kernel<false><<<128, 128, 0, s>>>(p.d_fmat);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  ptr9_kernel<<<p.C, kThreads, 0, s>>>(p.C, p.d_csr_ptr, p.d_ptr9);
   return cudaGetLastError();
 }
 
 cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
   p.threads = kThreads;
-  p.smem = dft_smem_bytes(p.A, p.A * p.S * p.S);
+  p.smem = dft_smem_bytes(p.A, p.gt.max_chan_entries);
   p.ent_in_smem = 1;
   cudaError_t e;
   switch (p.xform) {

@@ -110,11 +110,11 @@ __device__ __forceinline__ void fft_line(float2 (&v)[8], const float2 (&tw)[8], 
 
 // Shared-memory layout of the imaging kernel, in bytes from the base.
 struct FftSmem {
-  size_t R, scr, ptr, coef, E, autos, ent, total;
+  size_t R, scr, wst, coef, E, autos, ent_a, ent_w, total;
 };
 
 template <int N, int P>
-__host__ __device__ inline FftSmem fft_smem_layout(int A, int nnz, int ent_in_smem) {
+__host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int ent_in_smem) {
   using G = Geo<N>;
   FftSmem L;
   size_t o = 0;
@@ -125,11 +125,12 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int nnz, int ent_in_sm
   };
   L.R = take(sizeof(float2) * P * N * N);
   L.scr = take(sizeof(float2) * (G::THREADS / 32) * G::SCR);
-  L.ptr = take(sizeof(int) * (N * N + 1));
+  L.wst = take(sizeof(int) * 2 * (G::THREADS / 32) * 8);
   L.coef = take(sizeof(float2) * A * P);
-  L.E = take((P == 2 ? 16 : 8) * (size_t)A);
+  L.E = take((P == 2 ? 16 : 8) * (size_t)(A + 1));
   L.autos = take(sizeof(int4) * A);
-  L.ent = take(ent_in_smem ? sizeof(int2) * (size_t)nnz : 0);
+  L.ent_a = take(ent_in_smem ? sizeof(uint16_t) * (size_t)max_entries : 0);
+  L.ent_w = take(ent_in_smem ? sizeof(float) * (size_t)max_entries : 0);
   L.total = o;
   return L;
 }
@@ -137,8 +138,9 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int nnz, int ent_in_sm
 template <int N, int P>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     fft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
-                     const float2* __restrict__ coef, const int* __restrict__ csr_ptr,
-                     const int2* __restrict__ csr_ent, int nnz, int ent_in_smem,
+                     const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
+                     const int* __restrict__ g_off, const uint16_t* __restrict__ g_ent_a,
+                     const float* __restrict__ g_ent_w, int max_entries, int ent_in_smem,
                      const float2* __restrict__ twiddle, float* __restrict__ part, int* __restrict__ part_auto) {
   using G = Geo<N>;
   constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2;
@@ -146,15 +148,18 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
   constexpr int NPL = (P == 2) ? 4 : 1;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const FftSmem L = fft_smem_layout<N, P>(A, nnz, ent_in_smem);
+  constexpr int WARPS = NT / 32;
+  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem);
   float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
   float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
-  int* ptr_s = reinterpret_cast<int*>(smem + L.ptr);
+  int* cnt_s = reinterpret_cast<int*>(smem + L.wst);    // [warps][8] trip counts
+  int* base_s = cnt_s + WARPS * 8;                      // [warps][8] first entries
   float2* coef_s = reinterpret_cast<float2*>(smem + L.coef);
   float4* E4 = reinterpret_cast<float4*>(smem + L.E);
   float2* E2 = reinterpret_cast<float2*>(smem + L.E);
   int4* auto_s = reinterpret_cast<int4*>(smem + L.autos);
-  int2* ent_s = reinterpret_cast<int2*>(smem + L.ent);
+  uint16_t* enta_s = reinterpret_cast<uint16_t*>(smem + L.ent_a);
+  float* entw_s = reinterpret_cast<float*>(smem + L.ent_w);
 
   const int tid = threadIdx.x;
   const int line = tid / R1, n1 = tid % R1, r = line % G::RPW;
@@ -194,7 +199,9 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
   load_raw(u0, raw);
 
   int cur_c = -1;
-  const int2* ent = csr_ent;
+  const uint16_t* ent_a = g_ent_a;
+  const float* ent_w = g_ent_w;
+  const int warp = tid >> 5, lane = tid & 31;
 
   auto flush = [&](int c) {
     const int slot = c - c_first;
@@ -223,16 +230,23 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
           for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
       }
       cur_c = c;
-      const int* cp = csr_ptr + (size_t)c * (NN + 1);
-      for (int k = tid; k <= NN; k += NT) ptr_s[k] = cp[k];
+      if (tid < WARPS * 8) {
+        cnt_s[tid] = g_cnt[(size_t)c * WARPS * 8 + tid];
+        base_s[tid] = g_base[(size_t)c * WARPS * 8 + tid];
+      }
       for (int k = tid; k < A * P; k += NT) coef_s[k] = coef[(size_t)c * A * P + k];
       for (int a = tid; a < A; a += NT) auto_s[a] = make_int4(0, 0, 0, 0);
+      const int e0 = g_off[c], ne = g_off[c + 1] - e0;
       if (ent_in_smem) {
-        const int2* src = csr_ent + (size_t)c * nnz;
-        for (int k = tid; k < nnz; k += NT) ent_s[k] = src[k];
-        ent = ent_s;
+        for (int k = tid; k < ne; k += NT) {
+          enta_s[k] = g_ent_a[e0 + k];
+          entw_s[k] = g_ent_w[e0 + k];
+        }
+        ent_a = enta_s;
+        ent_w = entw_s;
       } else {
-        ent = csr_ent + (size_t)c * nnz;
+        ent_a = g_ent_a + e0;
+        ent_w = g_ent_w + e0;
       }
       __syncthreads();
     }
@@ -270,20 +284,21 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
       float2 v[P][8];
 #pragma unroll
       for (int n2 = 0; n2 < 8; ++n2) {
-        const int cell = y * N + n1 + R1 * n2;
-        const int e0 = ptr_s[cell], e1 = ptr_s[cell + 1];
+        // cell (y, n1 + R1 n2): lane-interleaved entries, warp-uniform trip count
+        const int K = cnt_s[warp * 8 + n2];
+        const int b = base_s[warp * 8 + n2] + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
-        for (int e = e0; e < e1; ++e) {
-          const int2 en = ent[e];
-          const float w = __int_as_float(en.y);
+        for (int k = 0; k < K; ++k) {
+          const int a = ent_a[b + 32 * k];
+          const float w = ent_w[b + 32 * k];
           if constexpr (P == 2) {
-            const float4 ev = E4[en.x];
+            const float4 ev = E4[a];
             gx.x = fmaf(w, ev.x, gx.x);
             gx.y = fmaf(w, ev.y, gx.y);
             gy.x = fmaf(w, ev.z, gy.x);
             gy.y = fmaf(w, ev.w, gy.y);
           } else {
-            const float2 ev = E2[en.x];
+            const float2 ev = E2[a];
             gx.x = fmaf(w, ev.x, gx.x);
             gx.y = fmaf(w, ev.y, gx.y);
           }
@@ -346,11 +361,11 @@ cudaError_t occupancy(int threads, size_t smem, int* per_sm) {
 }
 
 size_t smem_for(const Plan& p, int ent_in_smem) {
-  const int nnz = p.A * p.S * p.S;
-  if (p.N == 64) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, nnz, ent_in_smem).total
-                                 : fft_smem_layout<64, 1>(p.A, nnz, ent_in_smem).total;
-  return p.P == 2 ? fft_smem_layout<32, 2>(p.A, nnz, ent_in_smem).total
-                  : fft_smem_layout<32, 1>(p.A, nnz, ent_in_smem).total;
+  const int me = p.gt.max_chan_entries;
+  if (p.N == 64) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem).total
+                                 : fft_smem_layout<64, 1>(p.A, me, ent_in_smem).total;
+  return p.P == 2 ? fft_smem_layout<32, 2>(p.A, me, ent_in_smem).total
+                  : fft_smem_layout<32, 1>(p.A, me, ent_in_smem).total;
 }
 
 bool ent_fits(const Plan& p) {
@@ -405,12 +420,11 @@ cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
 }
 
 cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s) {
-  const int nnz = p.A * p.S * p.S;
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
-  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, \
-                                                                 p.d_coef, p.d_csr_ptr, p.d_csr_ent, nnz, ent,  \
-                                                                 p.d_twiddle, p.d_part, p.d_part_auto)
+  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
+      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
+      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
   } else {
@@ -422,12 +436,11 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
 
 cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                                 int* part_auto, cudaStream_t s) {
-  const int nnz = p.A * p.S * p.S;
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
-  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, \
-                                                                 p.d_coef, p.d_csr_ptr, p.d_csr_ent, nnz, ent,  \
-                                                                 p.d_twiddle, part, part_auto)
+  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
+      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
+      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, part, part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
   } else {

@@ -1,0 +1,164 @@
+// epic_gather.cu -- plan-time gather tables of the gridders.
+//
+// The gridding of Eq. (5) (W * E') is done as a gather: every grid cell sums
+// w * e over the antennas whose kernel box covers it (the per-cell table built
+// by build_csr_kernel, antenna order).  An imaging kernel thread owns 8 cells
+// ("slots"); the 32 threads of a warp walk their k-th entries in lock step.
+// This file lays those entries out for that walk: for warp w and slot s the
+// trip count K_ws is the largest cell count among the warp's 32 cells, and entry
+// k of lane l sits at base_ws + 32 k + l, cells with fewer entries padded with
+// weight-0 entries of antenna 0 (adding +0 leaves every sum unchanged, and the
+// real entries keep their antenna order, so the results are the same as a
+// per-cell loop).  Loads are coalesced and the loop has no divergence.
+//
+// Cell layouts (thread task t, slot s -> cell (y, x)):
+//   kFft64: y = t / 8, x = t % 8 + 8 s   (the FFT kernel's row layout, N = 64)
+//   kFft32: y = t / 4, x = t % 4 + 4 s   (N = 32)
+//   kChunk64: y = t / 8, x = 8 (t % 8) + s (eight consecutive cells, tensor path)
+// With sorting on, tasks are ordered by their number of entries (stable), so
+// warps get cells of similar load; thread i of a channel then works on task
+// task[i].
+#include "epic_internal.cuh"
+
+namespace epic {
+
+namespace {
+
+__device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
+  switch (layout) {
+    case kLayoutFft64: return make_int2(task >> 3, (task & 7) + 8 * s);
+    case kLayoutFft32: return make_int2(task >> 2, (task & 3) + 4 * s);
+    default: return make_int2(task >> 3, 8 * (task & 7) + s);
+  }
+}
+
+// One CTA of nt threads per channel.  fill = 0: only the padded entry count of
+// the channel (tot[c]); fill = 1: also every table.
+__global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int fill, const int* __restrict__ csr_ptr,
+                                     const int2* __restrict__ csr_ent, const int* __restrict__ chan_off,
+                                     int* __restrict__ tot, int* __restrict__ cnt_out, int* __restrict__ base_out,
+                                     uint16_t* __restrict__ task_out, uint16_t* __restrict__ ent_a,
+                                     float* __restrict__ ent_w) {
+  extern __shared__ int sh[];
+  const int nt = blockDim.x, warps = nt / 32;
+  int* keys = sh;                // [nt]
+  int* perm = sh + nt;           // [nt]
+  int* kws = perm + nt;          // [warps * 8]
+  int* bws = kws + warps * 8;    // [warps * 8]
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int* ptr = csr_ptr + (size_t)c * (N * N + 1);
+
+  int key = 0;
+  for (int s = 0; s < 8; ++s) {
+    const int2 yx = cell_of(layout, tid, s);
+    key += ptr[yx.x * N + yx.y + 1] - ptr[yx.x * N + yx.y];
+  }
+  int task = tid;
+  if (sorted) {
+    keys[tid] = key;
+    __syncthreads();
+    int rank = 0;
+    for (int j = 0; j < nt; ++j) rank += (keys[j] < key) || (keys[j] == key && j < tid);
+    perm[rank] = tid;
+    __syncthreads();
+    task = perm[tid];
+  }
+  int cnt[8], beg[8];
+  for (int s = 0; s < 8; ++s) {
+    const int2 yx = cell_of(layout, task, s);
+    beg[s] = ptr[yx.x * N + yx.y];
+    cnt[s] = ptr[yx.x * N + yx.y + 1] - beg[s];
+    const int k = __reduce_max_sync(0xffffffffu, cnt[s]);
+    if (lane == 0) kws[w * 8 + s] = k;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int q = 0; q < warps * 8; ++q) {
+      bws[q] = run;
+      run += 32 * kws[q];
+    }
+    if (!fill) tot[c] = run;
+  }
+  __syncthreads();
+  if (!fill) return;
+  const size_t off = (size_t)chan_off[c];
+  if (tid < warps * 8) {
+    cnt_out[(size_t)c * warps * 8 + tid] = kws[tid];
+    base_out[(size_t)c * warps * 8 + tid] = bws[tid];
+  }
+  task_out[(size_t)c * nt + tid] = (uint16_t)task;
+  const int2* ent = csr_ent + (size_t)c * nnz;
+  for (int s = 0; s < 8; ++s) {
+    const int K = kws[w * 8 + s];
+    for (int k = 0; k < K; ++k) {
+      const size_t idx = off + (size_t)bws[w * 8 + s] + 32 * k + lane;
+      if (k < cnt[s]) {
+        const int2 e = ent[beg[s] + k];
+        ent_a[idx] = (uint16_t)e.x;
+        ent_w[idx] = __int_as_float(e.y);
+      } else {
+        ent_a[idx] = 0;
+        ent_w[idx] = 0.f;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, size_t* total_bytes) {
+  GatherTables& g = p.gt;
+  g.layout = layout;
+  g.threads = threads;
+  g.sorted = sorted;
+  const int warps = threads / 32;
+  const int nnz = p.A * p.S * p.S;
+  const size_t smem = sizeof(int) * (2 * (size_t)threads + 2 * (size_t)warps * 8);
+  int* d_tot = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * p.C);
+  if (e != cudaSuccess) return e;
+  gather_tables_kernel<<<p.C, threads, smem>>>(layout, p.N, nnz, sorted, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
+                                               nullptr, nullptr, nullptr, nullptr, nullptr);
+  e = cudaGetLastError();
+  std::vector<int> tot(p.C);
+  if (e == cudaSuccess) e = cudaMemcpy(tot.data(), d_tot, sizeof(int) * p.C, cudaMemcpyDeviceToHost);
+  cudaFree(d_tot);
+  if (e != cudaSuccess) return e;
+  std::vector<int> off(p.C + 1, 0);
+  g.max_chan_entries = 0;
+  for (int c = 0; c < p.C; ++c) {
+    off[c + 1] = off[c] + tot[c];
+    if (tot[c] > g.max_chan_entries) g.max_chan_entries = tot[c];
+  }
+  const size_t total = (size_t)off[p.C];
+  size_t bytes = 0;
+  auto grab = [&](void** ptr, size_t b) {
+    cudaError_t err = cudaMalloc(ptr, b > 0 ? b : 16);
+    if (err == cudaSuccess) bytes += b;
+    return err;
+  };
+  if ((e = grab(reinterpret_cast<void**>(&g.d_chan_off), sizeof(int) * (p.C + 1))) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_cnt), sizeof(int) * (size_t)p.C * warps * 8)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_base), sizeof(int) * (size_t)p.C * warps * 8)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_task), sizeof(uint16_t) * (size_t)p.C * threads)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_ent_a), sizeof(uint16_t) * total)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_ent_w), sizeof(float) * total)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (p.C + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  gather_tables_kernel<<<p.C, threads, smem>>>(layout, p.N, nnz, sorted, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
+                                               nullptr, g.d_cnt, g.d_base, g.d_task, g.d_ent_a, g.d_ent_w);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  *total_bytes = bytes;
+  return e;
+}
+
+void free_gather_tables(GatherTables& g) {
+  void* ptrs[] = {g.d_cnt, g.d_base, g.d_chan_off, g.d_ent_a, g.d_ent_w, g.d_task};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  g = GatherTables();
+}
+
+}  // namespace epic

@@ -24,6 +24,19 @@ struct WorkSplit {
   int T;
 };
 
+// Gather tables of a gridder (see epic_gather.cu).
+enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2 };
+struct GatherTables {
+  int layout = 0, threads = 0, sorted = 0;
+  int max_chan_entries = 0;      // padded entries of the largest channel
+  int* d_cnt = nullptr;          // [C][warps][8] trip count of (warp, slot)
+  int* d_base = nullptr;         // [C][warps][8] first entry of (warp, slot) within the channel
+  int* d_chan_off = nullptr;     // [C+1] first entry of each channel
+  uint16_t* d_task = nullptr;    // [C][threads] task (cell group) of each thread
+  uint16_t* d_ent_a = nullptr;   // [entries] antenna index (0 for padding)
+  float* d_ent_w = nullptr;      // [entries] kernel weight (0 for padding)
+};
+
 struct Plan {
   // descriptor copy
   int A, P, C, N, S, xform, subtract;
@@ -46,8 +59,8 @@ struct Plan {
   int2* d_csr_ent = nullptr;    // [C][A*S*S] (antenna, weight bits), antenna order
   float2* d_twiddle = nullptr;  // [N] exp(+2 pi i m / N)
   uint16_t* d_fmat = nullptr;   // tensor path: real DFT matrix, hi/lo 16-bit, shared-memory image (64 KB)
-  int* d_ptr9 = nullptr;        // tensor path: [C][9][512] thread-major gather row pointers
   int* d_status = nullptr;      // device error word
+  GatherTables gt;              // gridder's lane-interleaved gather tables
 
   // imaging launch shape and its workspace (partial images per CTA span)
   int ctas = 0, threads = 0, spans = 0, ent_in_smem = 0;
@@ -78,6 +91,9 @@ struct Plan {
 cudaError_t launch_plan_terms(Plan& p, cudaStream_t s);
 cudaError_t launch_build_csr(Plan& p, cudaStream_t s);
 cudaError_t launch_twiddles(Plan& p, cudaStream_t s);
+// Builds p.gt from the per-cell table (two launches, synchronous).
+cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, size_t* bytes);
+void free_gather_tables(GatherTables& g);
 
 // FP32 FFT path: the fused unpack + calibrate + grid + FFT + products kernel.
 // Sets p.threads, p.smem, p.ent_in_smem and returns the resident CTAs per SM.
@@ -86,8 +102,7 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
                              cudaStream_t s);
 
 // Tensor-core path (DFT-by-GEMM on tcgen05; N = 64, two polarisations).
-bool dft_supported(int N, int P, int A, int S);
-size_t dft_smem_need(int A, int S);
+size_t dft_smem_need(int A, int max_entries);
 cudaError_t launch_dft_tables(Plan& p, cudaStream_t s);
 cudaError_t dft_image_config(Plan& p, int* ctas_per_sm);
 cudaError_t launch_dft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
