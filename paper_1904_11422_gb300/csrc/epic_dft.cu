@@ -392,29 +392,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     //    stage-1 B operand, split into 16-bit hi/lo parts (the previous sample's
     //    stage-1 products, which read this buffer, completed before its conversion)
     {
-      // the 8 cells of this task walked together (independent load/FMA chains
-      // overlap); lane-interleaved entries, warp-uniform trip count per cell
       float gre[2][8], gim[2][8];
-      int K[8], B[8], kmax = 0;
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
-        K[s] = cnt_s[warp * 8 + s];
-        B[s] = base_s[warp * 8 + s] + lane;
-        kmax = max(kmax, K[s]);
-        gre[0][s] = gim[0][s] = gre[1][s] = gim[1][s] = 0.f;
-      }
-      for (int k = 0; k < kmax; ++k) {
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          if (k < K[s]) {
-            const float w = entw_s[B[s] + 32 * k];
-            const float4 ev = E4[enta_s[B[s] + 32 * k]];
-            gre[0][s] = fmaf(w, ev.x, gre[0][s]);
-            gim[0][s] = fmaf(w, ev.y, gim[0][s]);
-            gre[1][s] = fmaf(w, ev.z, gre[1][s]);
-            gim[1][s] = fmaf(w, ev.w, gim[1][s]);
-          }
+        // lane-interleaved entries of cell (y, 8q + s), warp-uniform trip count
+        const int K = cnt_s[warp * 8 + s];
+        const int b = base_s[warp * 8 + s] + lane;
+        float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
+        for (int k = 0; k < K; ++k) {
+          const float w = entw_s[b + 32 * k];
+          const float4 ev = E4[enta_s[b + 32 * k]];
+          xr = fmaf(w, ev.x, xr);
+          xi = fmaf(w, ev.y, xi);
+          yr = fmaf(w, ev.z, yr);
+          yi = fmaf(w, ev.w, yi);
         }
+        gre[0][s] = xr; gim[0][s] = xi; gre[1][s] = yr; gim[1][s] = yi;
       }
 #pragma unroll
       for (int g = 0; g < 2; ++g) {

@@ -282,37 +282,29 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     {
       const int y = line;
       float2 v[P][8];
-      // the 8 cells (y, n1 + R1 n2) of this thread, walked together so that
-      // their independent load/FMA chains overlap; entries are lane-interleaved
-      // with a warp-uniform trip count per cell
-      int K[8], B[8], kmax = 0;
 #pragma unroll
       for (int n2 = 0; n2 < 8; ++n2) {
-        K[n2] = cnt_s[warp * 8 + n2];
-        B[n2] = base_s[warp * 8 + n2] + lane;
-        kmax = max(kmax, K[n2]);
-        v[0][n2] = make_float2(0.f, 0.f);
-        if constexpr (P == 2) v[1][n2] = make_float2(0.f, 0.f);
-      }
-      for (int k = 0; k < kmax; ++k) {
-#pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) {
-          if (k < K[n2]) {
-            const int a = ent_a[B[n2] + 32 * k];
-            const float w = ent_w[B[n2] + 32 * k];
-            if constexpr (P == 2) {
-              const float4 ev = E4[a];
-              v[0][n2].x = fmaf(w, ev.x, v[0][n2].x);
-              v[0][n2].y = fmaf(w, ev.y, v[0][n2].y);
-              v[1][n2].x = fmaf(w, ev.z, v[1][n2].x);
-              v[1][n2].y = fmaf(w, ev.w, v[1][n2].y);
-            } else {
-              const float2 ev = E2[a];
-              v[0][n2].x = fmaf(w, ev.x, v[0][n2].x);
-              v[0][n2].y = fmaf(w, ev.y, v[0][n2].y);
-            }
+        // cell (y, n1 + R1 n2): lane-interleaved entries, warp-uniform trip count
+        const int K = cnt_s[warp * 8 + n2];
+        const int b = base_s[warp * 8 + n2] + lane;
+        float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
+        for (int k = 0; k < K; ++k) {
+          const int a = ent_a[b + 32 * k];
+          const float w = ent_w[b + 32 * k];
+          if constexpr (P == 2) {
+            const float4 ev = E4[a];
+            gx.x = fmaf(w, ev.x, gx.x);
+            gx.y = fmaf(w, ev.y, gx.y);
+            gy.x = fmaf(w, ev.z, gy.x);
+            gy.y = fmaf(w, ev.w, gy.y);
+          } else {
+            const float2 ev = E2[a];
+            gx.x = fmaf(w, ev.x, gx.x);
+            gx.y = fmaf(w, ev.y, gx.y);
           }
         }
+        v[0][n2] = gx;
+        if constexpr (P == 2) v[1][n2] = gy;
       }
       const int sw = G::swz(y);
 #pragma unroll
