@@ -268,7 +268,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
     total += gt_bytes;
     EPIC_TRY(epic::fft_image_config(p, &per_sm));
   } else {
-    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutChunk64, 512, 1, &gt_bytes));
+    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutPair64, 512, 0, &gt_bytes));
     total += gt_bytes;
     if (epic::dft_smem_need(p.A, p.gt.max_chan_entries) > kSmemOptin) {
       free_plan(p);

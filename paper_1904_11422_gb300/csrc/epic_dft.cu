@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint32_t ph1 = 0, ph2 = 0, pend1 = 0, pend2 = 0;
   int d2buf = 0, have_prev = 0, prev_buf = 0;
-  int gy = 0, gq = 0;                                    // gridder task: row y, cells x = 8q..8q+7
+  int pair[4] = {0, 0, 0, 0};                            // gridder: four cell pairs (y, 2r..2r+1), index y*32 + r
   const int ej = 16 * lg + (lane >> 1), ec = lane & 1;   // epilogue lanes (j, c) of D2
   const int ck = 16 * lg + (lane >> 1), cc = lane & 1;   // conversion lanes (k, c) of D1
   const int cg = cq >> 1, cy0 = 32 * (cq & 1);           // conversion columns (g, y0 .. y0+31)
@@ -362,9 +362,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         enta_s[k] = g_ent_a[e0 + k];
         entw_s[k] = g_ent_w[e0 + k];
       }
-      const int task = g_task[(size_t)c * kThreads + tid];
-      gy = task >> 3;
-      gq = task & 7;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pair[j] = g_task[((size_t)c * kThreads + tid) * 4 + j];
       __syncthreads();
     }
 
@@ -388,14 +387,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
-    // 2. grid cells (y, 8q..8q+7) of both polarisations into rows (g, y) of the
-    //    stage-1 B operand, split into 16-bit hi/lo parts (the previous sample's
-    //    stage-1 products, which read this buffer, completed before its conversion)
+    // 2. grid the thread's four cell pairs (y, 2r..2r+1) of both polarisations
+    //    into rows (g, y) of the stage-1 B operand, split into 16-bit hi/lo parts
+    //    (the previous sample's stage-1 products, which read this buffer,
+    //    completed before its conversion)
     {
       float gre[2][8], gim[2][8];
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
-        // lane-interleaved entries of cell (y, 8q + s), warp-uniform trip count
+        // slot s = cell (s & 1) of pair s >> 1: lane-interleaved entries, warp-uniform trip count
         const int K = cnt_s[warp * 8 + s];
         const int b = base_s[warp * 8 + s] + lane;
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
@@ -410,24 +410,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         gre[0][s] = xr; gim[0][s] = xi; gre[1][s] = yr; gim[1][s] = yi;
       }
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const uint32_t off = slab_off(g * kN + gy, 8 * gq);
+      for (int j = 0; j < 4; ++j) {
+        const int y = pair[j] >> 5, x = 2 * (pair[j] & 31);
 #pragma unroll
-        for (int comp = 0; comp < 2; ++comp) {
-          const float* v = comp ? gim[g] : gre[g];
-          uint32_t hi[4], lo[4];
+        for (int g = 0; g < 2; ++g) {
+          const uint32_t off = slab_off(g * kN + y, x);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            hi[q] = pack2<kBf>(v[2 * q], v[2 * q + 1]);
+          for (int comp = 0; comp < 2; ++comp) {
+            const float* v = comp ? gim[g] : gre[g];
+            const uint32_t hi = pack2<kBf>(v[2 * j], v[2 * j + 1]);
+            *reinterpret_cast<uint32_t*>(sm + DftSmem::B1 + comp * kSlab + off) = hi;
             if constexpr (Pr::kSplit) {
-              const float2 back = unpack2<kBf>(hi[q]);
-              lo[q] = pack2<kBf>(v[2 * q] - back.x, v[2 * q + 1] - back.y);
+              const float2 back = unpack2<kBf>(hi);
+              *reinterpret_cast<uint32_t*>(sm + DftSmem::B1 + (2 + comp) * kSlab + off) =
+                  pack2<kBf>(v[2 * j] - back.x, v[2 * j + 1] - back.y);
             }
           }
-          *reinterpret_cast<uint4*>(sm + DftSmem::B1 + comp * kSlab + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          if constexpr (Pr::kSplit)
-            *reinterpret_cast<uint4*>(sm + DftSmem::B1 + (2 + comp) * kSlab + off) =
-                make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
     }

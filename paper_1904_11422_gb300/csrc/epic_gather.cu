@@ -14,7 +14,8 @@
 // Cell layouts (thread task t, slot s -> cell (y, x)):
 //   kFft64: y = t / 8, x = t % 8 + 8 s   (the FFT kernel's row layout, N = 64)
 //   kFft32: y = t / 4, x = t % 4 + 4 s   (N = 32)
-//   kChunk64: y = t / 8, x = 8 (t % 8) + s (eight consecutive cells, tensor path)
+//   kChunk64: y = t / 8, x = 8 (t % 8) + s (eight consecutive cells)
+//   kPair64: four load-balanced cell pairs per thread (tensor path, see deal_pairs)
 // With sorting on, tasks are ordered by their number of entries (stable), so
 // warps get cells of similar load; thread i of a channel then works on task
 // task[i].
@@ -32,6 +33,29 @@ __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
   }
 }
 
+// kLayoutPair64: the 2048 cell pairs (y, 2r..2r+1) of a 64 x 64 grid, ranked by
+// their number of entries (descending, ties by index) and dealt to the 512
+// threads in snake order, four per thread: thread t gets the pairs of rank
+// j*512 + t (j even) or j*512 + 511 - t (j odd), j = 0..3, so every thread's
+// total is close to the mean.  Slot s of the thread is cell (s & 1) of its pair
+// s >> 1.  pair_of[t*4 + j] receives pair index y*32 + r.
+__device__ void deal_pairs(const int* ptr, int tid, int* loads, int* perm, int* pair_of) {
+  for (int q = tid; q < 2048; q += 512) {
+    const int y = q >> 5, r = q & 31, cell = y * 64 + 2 * r;
+    loads[q] = ptr[cell + 2] - ptr[cell];
+  }
+  __syncthreads();
+  for (int q = tid; q < 2048; q += 512) {
+    const int L = loads[q];
+    int rank = 0;
+    for (int j = 0; j < 2048; ++j) rank += (loads[j] > L) || (loads[j] == L && j < q);
+    perm[rank] = q;
+  }
+  __syncthreads();
+  for (int j = 0; j < 4; ++j) pair_of[tid * 4 + j] = perm[j * 512 + ((j & 1) ? 511 - tid : tid)];
+  __syncthreads();
+}
+
 // One CTA of nt threads per channel.  fill = 0: only the padded entry count of
 // the channel (tot[c]); fill = 1: also every table.
 __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int fill, const int* __restrict__ csr_ptr,
@@ -41,31 +65,42 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
                                      float* __restrict__ ent_w) {
   extern __shared__ int sh[];
   const int nt = blockDim.x, warps = nt / 32;
-  int* keys = sh;                // [nt]
-  int* perm = sh + nt;           // [nt]
-  int* kws = perm + nt;          // [warps * 8]
+  int* kws = sh;                 // [warps * 8]
   int* bws = kws + warps * 8;    // [warps * 8]
+  int* keys = bws + warps * 8;   // [nt], or [2048] for pairs
+  int* perm = keys + (layout == kLayoutPair64 ? 2048 : nt);   // [nt], or [2048]
+  int* pair_of = perm + (layout == kLayoutPair64 ? 2048 : nt);  // [4 nt] (pairs only)
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int* ptr = csr_ptr + (size_t)c * (N * N + 1);
 
-  int key = 0;
-  for (int s = 0; s < 8; ++s) {
-    const int2 yx = cell_of(layout, tid, s);
-    key += ptr[yx.x * N + yx.y + 1] - ptr[yx.x * N + yx.y];
-  }
   int task = tid;
-  if (sorted) {
-    keys[tid] = key;
-    __syncthreads();
-    int rank = 0;
-    for (int j = 0; j < nt; ++j) rank += (keys[j] < key) || (keys[j] == key && j < tid);
-    perm[rank] = tid;
-    __syncthreads();
-    task = perm[tid];
+  int2 cells[8];
+  if (layout == kLayoutPair64) {
+    deal_pairs(ptr, tid, keys, perm, pair_of);
+    for (int s = 0; s < 8; ++s) {
+      const int q = pair_of[tid * 4 + (s >> 1)];
+      cells[s] = make_int2(q >> 5, 2 * (q & 31) + (s & 1));
+    }
+  } else {
+    int key = 0;
+    for (int s = 0; s < 8; ++s) {
+      const int2 yx = cell_of(layout, tid, s);
+      key += ptr[yx.x * N + yx.y + 1] - ptr[yx.x * N + yx.y];
+    }
+    if (sorted) {
+      keys[tid] = key;
+      __syncthreads();
+      int rank = 0;
+      for (int j = 0; j < nt; ++j) rank += (keys[j] < key) || (keys[j] == key && j < tid);
+      perm[rank] = tid;
+      __syncthreads();
+      task = perm[tid];
+    }
+    for (int s = 0; s < 8; ++s) cells[s] = cell_of(layout, task, s);
   }
   int cnt[8], beg[8];
   for (int s = 0; s < 8; ++s) {
-    const int2 yx = cell_of(layout, task, s);
+    const int2 yx = cells[s];
     beg[s] = ptr[yx.x * N + yx.y];
     cnt[s] = ptr[yx.x * N + yx.y + 1] - beg[s];
     const int k = __reduce_max_sync(0xffffffffu, cnt[s]);
@@ -87,7 +122,11 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
     cnt_out[(size_t)c * warps * 8 + tid] = kws[tid];
     base_out[(size_t)c * warps * 8 + tid] = bws[tid];
   }
-  task_out[(size_t)c * nt + tid] = (uint16_t)task;
+  if (layout == kLayoutPair64) {
+    for (int j = 0; j < 4; ++j) task_out[((size_t)c * nt + tid) * 4 + j] = (uint16_t)pair_of[tid * 4 + j];
+  } else {
+    task_out[(size_t)c * nt + tid] = (uint16_t)task;
+  }
   const int2* ent = csr_ent + (size_t)c * nnz;
   for (int s = 0; s < 8; ++s) {
     const int K = kws[w * 8 + s];
@@ -114,7 +153,8 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   g.sorted = sorted;
   const int warps = threads / 32;
   const int nnz = p.A * p.S * p.S;
-  const size_t smem = sizeof(int) * (2 * (size_t)threads + 2 * (size_t)warps * 8);
+  const size_t smem = sizeof(int) * (2 * (size_t)warps * 8 +
+                                     (layout == kLayoutPair64 ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));
   int* d_tot = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * p.C);
   if (e != cudaSuccess) return e;
@@ -141,7 +181,10 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   if ((e = grab(reinterpret_cast<void**>(&g.d_chan_off), sizeof(int) * (p.C + 1))) != cudaSuccess) return e;
   if ((e = grab(reinterpret_cast<void**>(&g.d_cnt), sizeof(int) * (size_t)p.C * warps * 8)) != cudaSuccess) return e;
   if ((e = grab(reinterpret_cast<void**>(&g.d_base), sizeof(int) * (size_t)p.C * warps * 8)) != cudaSuccess) return e;
-  if ((e = grab(reinterpret_cast<void**>(&g.d_task), sizeof(uint16_t) * (size_t)p.C * threads)) != cudaSuccess) return e;
+  const size_t per_thread = (layout == kLayoutPair64) ? 4 : 1;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_task), sizeof(uint16_t) * (size_t)p.C * threads * per_thread)) !=
+      cudaSuccess)
+    return e;
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_a), sizeof(uint16_t) * total)) != cudaSuccess) return e;
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_w), sizeof(float) * total)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (p.C + 1), cudaMemcpyHostToDevice)) != cudaSuccess)

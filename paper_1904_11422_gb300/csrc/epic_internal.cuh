@@ -25,14 +25,14 @@ struct WorkSplit {
 };
 
 // Gather tables of a gridder (see epic_gather.cu).
-enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2 };
+enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3 };
 struct GatherTables {
   int layout = 0, threads = 0, sorted = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel
   int* d_cnt = nullptr;          // [C][warps][8] trip count of (warp, slot)
   int* d_base = nullptr;         // [C][warps][8] first entry of (warp, slot) within the channel
   int* d_chan_off = nullptr;     // [C+1] first entry of each channel
-  uint16_t* d_task = nullptr;    // [C][threads] task (cell group) of each thread
+  uint16_t* d_task = nullptr;    // [C][threads] task of each thread ([C][threads][4] pairs for kLayoutPair64)
   uint16_t* d_ent_a = nullptr;   // [entries] antenna index (0 for padding)
   float* d_ent_w = nullptr;      // [entries] kernel weight (0 for padding)
 };
