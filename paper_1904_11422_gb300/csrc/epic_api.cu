@@ -31,7 +31,7 @@ bool grid_supported(int xform, int N, int P, int A, int S) {
   // tensor path: 64 x 64 grids of two polarisations, with the gather entries in
   // shared memory (bounded here by the unpadded count A S^2; the exact padded
   // count is checked when the plan is created)
-  return N == 64 && P == 2 && epic::dft_smem_need(A, A * S * S) <= kSmemOptin;
+  return N == 64 && P == 2 && A <= 512 && epic::dft_smem_need(A, A * S * S) <= kSmemOptin;
 }
 
 epic_status from_cuda(cudaError_t e) {

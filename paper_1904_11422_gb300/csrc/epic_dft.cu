@@ -332,9 +332,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int a = tid; a < A; a += kThreads) pa[a] = auto_s[a];
   };
 
+  // the two bytes of the thread's antenna (a = tid < A <= 512), prefetched one
+  // sample ahead so that the unpack never waits for HBM
+  auto load_raw = [&](long long u) -> unsigned {
+    const int c = (int)(u / T), t = (int)(u % T);
+    const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * 2;
+    return tid < A ? (unsigned)__ldg(reinterpret_cast<const unsigned short*>(base) + tid) : 0u;
+  };
+  unsigned raw = load_raw(u0), raw_next = 0;
+
   int cur_c = -1;
   for (long long u = u0; u < u1; ++u) {
-    const int c = (int)(u / T), t = (int)(u % T);
+    const int c = (int)(u / T);
     if (c != cur_c) {
       if (have_prev) {  // the last sample of the previous channel still owes its squares
         wait_or_abort(bar2, ph2, pend2);
@@ -367,11 +376,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
     }
 
+    if (u + 1 < u1) raw_next = load_raw(u + 1);
+
     // 1. unpack, calibrate, exact integer self powers
     {
-      const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * 2;
-      for (int a = tid; a < A; a += kThreads) {
-        const unsigned raw = __ldg(reinterpret_cast<const unsigned short*>(base) + a);
+      const int a = tid;
+      if (a < A) {
         const int xr = nib_hi(raw & 0xffu), xi = nib_lo(raw & 0xffu);
         const int yr = nib_hi(raw >> 8), yi = nib_lo(raw >> 8);
         const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
@@ -512,6 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     have_prev = 1;
     prev_buf = d2buf;
     d2buf ^= 1;
+    raw = raw_next;
   }
   if (!*abort_flag) {
     if (have_prev) {
