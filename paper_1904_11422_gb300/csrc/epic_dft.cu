@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
                      const int* __restrict__ g_off, const uint16_t* __restrict__ g_task,
                      const uint16_t* __restrict__ g_ent_a, const float* __restrict__ g_ent_w, int max_entries,
-                     int erep, const uint32_t* __restrict__ fmat, float* __restrict__ part,
-                     int* __restrict__ part_auto, int* __restrict__ status) {
+                     const uint32_t* __restrict__ fmat, float* __restrict__ part, int* __restrict__ part_auto,
+                     int* __restrict__ status) {
   using Pr = Prec<XF>;
   constexpr bool kBf = Pr::kBf16;
   constexpr int NN = kN * kN;
@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t raw_addr = smem_u32(smem_raw);
   unsigned char* sm = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(sm);
-  float4* E4 = reinterpret_cast<float4*>(sm + DftSmem::E);  // [A][erep] replicated fields
-  float2* coef_s = reinterpret_cast<float2*>(E4 + A * erep); // [A][2]
+  float4* E4 = reinterpret_cast<float4*>(sm + DftSmem::E);
+  float2* coef_s = reinterpret_cast<float2*>(E4 + A);       // [A][2]
   int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A);    // [A]
   int* cnt_s = reinterpret_cast<int*>(auto_s + A);           // [16 warps][8] trip counts
   int* base_s = cnt_s + 16 * 8;                              // [16 warps][8] first entries
@@ -385,9 +385,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int xr = nib_hi(raw & 0xffu), xi = nib_lo(raw & 0xffu);
         const int yr = nib_hi(raw >> 8), yi = nib_lo(raw >> 8);
         const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
-        const float4 e4 = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
-                                      ky.x * yi + ky.y * yr);
-        for (int j = 0; j < erep; ++j) E4[a * erep + j] = e4;
+        E4[a] = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
+                            ky.x * yi + ky.y * yr);
         int4 au = auto_s[a];
         au.x += xr * xr + xi * xi;
         au.y += yr * yr + yi * yi;
@@ -412,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
         for (int k = 0; k < K; ++k) {
           const float w = entw_s[b + 32 * k];
-          const float4 ev = E4[enta_s[b + 32 * k] * erep + (lane & (erep - 1))];
+          const float4 ev = E4[enta_s[b + 32 * k]];
           xr = fmaf(w, ev.x, xr);
           xi = fmaf(w, ev.y, xi);
           yr = fmaf(w, ev.z, yr);
@@ -576,9 +575,9 @@ __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
   out[(size_t)128 * 128 + (size_t)m * 128 + kk] = lo;
 }
 
-size_t dft_smem_bytes(int A, int max_entries, int erep) {
+size_t dft_smem_bytes(int A, int max_entries) {
   size_t b = 8 * (size_t)kSlab;            // the two B operands (gridded fields, stage-1 result)
-  b += 16 * (size_t)A * erep + 16 * (size_t)A + 16 * (size_t)A;  // E (replicated), coefficients, self powers
+  b += 16 * (size_t)A + 16 * (size_t)A + 16 * (size_t)A;  // E, coefficients, self powers
   b += 2 * 16 * 8 * sizeof(int);            // gather trip counts and bases
   b += 32;                                  // two mbarriers, TMEM address, abort flag
   b += 6 * (size_t)max_entries;             // gather entries (weight, antenna)
@@ -590,8 +589,8 @@ cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkS
                        int* part_auto, cudaStream_t s) {
   dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(
       d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-      p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.erep,
-      reinterpret_cast<const uint32_t*>(p.d_fmat), part, part_auto, p.d_status);
+      p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, reinterpret_cast<const uint32_t*>(p.d_fmat),
+      part, part_auto, p.d_status);
   return cudaGetLastError();
 }
 
@@ -604,7 +603,7 @@ cudaError_t dft_attr(size_t smem) {
 
 // Shared memory the tensor kernel needs for a plan whose largest channel has
 // max_entries padded gather entries.
-size_t dft_smem_need(int A, int max_entries) { return dft_smem_bytes(A, max_entries, 1); }
+size_t dft_smem_need(int A, int max_entries) { return dft_smem_bytes(A, max_entries); }
 
 cudaError_t launch_dft_tables(Plan& p, cudaStream_t s) {
   if (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_BF16)
@@ -616,12 +615,7 @@ cudaError_t launch_dft_tables(Plan& p, cudaStream_t s) {
 
 cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
   p.threads = kThreads;
-  // 8 copies of every field (one per bank group of a 16-byte load phase) when they fit
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  p.erep = dft_smem_bytes(p.A, p.gt.max_chan_entries, 8) <= (size_t)optin ? 8 : 1;
-  p.smem = dft_smem_bytes(p.A, p.gt.max_chan_entries, p.erep);
+  p.smem = dft_smem_bytes(p.A, p.gt.max_chan_entries);
   p.ent_in_smem = 1;
   cudaError_t e;
   switch (p.xform) {

@@ -113,11 +113,8 @@ struct FftSmem {
   size_t R, scr, wst, coef, E, autos, ent_a, ent_w, total;
 };
 
-// erep: copies of each antenna's calibrated field in shared memory (one per
-// bank group of a load phase, so that gathers by different lanes never
-// conflict); 1 when they do not fit.
 template <int N, int P>
-__host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int ent_in_smem, int erep) {
+__host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int ent_in_smem) {
   using G = Geo<N>;
   FftSmem L;
   size_t o = 0;
@@ -130,7 +127,7 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int e
   L.scr = take(sizeof(float2) * (G::THREADS / 32) * G::SCR);
   L.wst = take(sizeof(int) * 2 * (G::THREADS / 32) * 8);
   L.coef = take(sizeof(float2) * A * P);
-  L.E = take((P == 2 ? 16 : 8) * (size_t)(A + 1) * erep);
+  L.E = take((P == 2 ? 16 : 8) * (size_t)(A + 1));
   L.autos = take(sizeof(int4) * A);
   L.ent_a = take(ent_in_smem ? sizeof(uint16_t) * (size_t)max_entries : 0);
   L.ent_w = take(ent_in_smem ? sizeof(float) * (size_t)max_entries : 0);
@@ -143,7 +140,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     fft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
                      const int* __restrict__ g_off, const uint16_t* __restrict__ g_ent_a,
-                     const float* __restrict__ g_ent_w, int max_entries, int ent_in_smem, int erep,
+                     const float* __restrict__ g_ent_w, int max_entries, int ent_in_smem,
                      const float2* __restrict__ twiddle, float* __restrict__ part, int* __restrict__ part_auto) {
   using G = Geo<N>;
   constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2;
@@ -152,7 +149,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int WARPS = NT / 32;
-  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem, erep);
+  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem);
   float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
   float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
   int* cnt_s = reinterpret_cast<int*>(smem + L.wst);    // [warps][8] trip counts
@@ -205,7 +202,6 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
   const uint16_t* ent_a = g_ent_a;
   const float* ent_w = g_ent_w;
   const int warp = tid >> 5, lane = tid & 31;
-  const int ecopy = lane & (erep - 1);  // this lane's copy of the fields
 
   auto flush = [&](int c) {
     const int slot = c - c_first;
@@ -270,13 +266,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
           const int yr = nib_hi(raw[k] >> 8), yi = nib_lo(raw[k] >> 8);
           const float2 ky = coef_s[a * P + 1];
           const float2 ey = make_float2(ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
-          const float4 e4 = make_float4(ex.x, ex.y, ey.x, ey.y);
-          for (int j = 0; j < erep; ++j) E4[a * erep + j] = e4;
+          E4[a] = make_float4(ex.x, ex.y, ey.x, ey.y);
           au.y += yr * yr + yi * yi;
           au.z += xr * yr + xi * yi;
           au.w += xi * yr - xr * yi;
         } else {
-          for (int j = 0; j < erep; ++j) E2[a * erep + j] = ex;
+          E2[a] = ex;
         }
         auto_s[a] = au;
       }
@@ -297,13 +292,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
           const int a = ent_a[b + 32 * k];
           const float w = ent_w[b + 32 * k];
           if constexpr (P == 2) {
-            const float4 ev = E4[a * erep + ecopy];
+            const float4 ev = E4[a];
             gx.x = fmaf(w, ev.x, gx.x);
             gx.y = fmaf(w, ev.y, gx.y);
             gy.x = fmaf(w, ev.z, gy.x);
             gy.y = fmaf(w, ev.w, gy.y);
           } else {
-            const float2 ev = E2[a * erep + ecopy];
+            const float2 ev = E2[a];
             gx.x = fmaf(w, ev.x, gx.x);
             gx.y = fmaf(w, ev.y, gx.y);
           }
@@ -365,19 +360,19 @@ cudaError_t occupancy(int threads, size_t smem, int* per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fft_image_kernel<N, P>, threads, smem);
 }
 
-size_t smem_for(const Plan& p, int ent_in_smem, int erep) {
+size_t smem_for(const Plan& p, int ent_in_smem) {
   const int me = p.gt.max_chan_entries;
-  if (p.N == 64) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem, erep).total
-                                 : fft_smem_layout<64, 1>(p.A, me, ent_in_smem, erep).total;
-  return p.P == 2 ? fft_smem_layout<32, 2>(p.A, me, ent_in_smem, erep).total
-                  : fft_smem_layout<32, 1>(p.A, me, ent_in_smem, erep).total;
+  if (p.N == 64) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem).total
+                                 : fft_smem_layout<64, 1>(p.A, me, ent_in_smem).total;
+  return p.P == 2 ? fft_smem_layout<32, 2>(p.A, me, ent_in_smem).total
+                  : fft_smem_layout<32, 1>(p.A, me, ent_in_smem).total;
 }
 
-size_t smem_optin() {
+bool ent_fits(const Plan& p) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return (size_t)optin;
+  return smem_for(p, 1) <= (size_t)optin;
 }
 
 // The gridding step alone, for the debug entry point: the same gather table,
@@ -415,12 +410,8 @@ __global__ void debug_grid_kernel(const uint8_t* __restrict__ volts, int T, int 
 }  // namespace
 
 cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
-  // prefer entries in shared memory, then replicated fields (128 B per antenna)
-  const size_t cap = smem_optin();
-  const int full_rep = 128 / (p.P == 2 ? 16 : 8);
-  p.ent_in_smem = smem_for(p, 1, 1) <= cap ? 1 : 0;
-  p.erep = smem_for(p, p.ent_in_smem, full_rep) <= cap ? full_rep : 1;
-  p.smem = smem_for(p, p.ent_in_smem, p.erep);
+  p.ent_in_smem = ent_fits(p) ? 1 : 0;
+  p.smem = smem_for(p, p.ent_in_smem);
   p.threads = (p.N == 64) ? Geo<64>::THREADS : Geo<32>::THREADS;
   if (p.N == 64) return p.P == 2 ? occupancy<64, 2>(p.threads, p.smem, ctas_per_sm)
                                  : occupancy<64, 1>(p.threads, p.smem, ctas_per_sm);
@@ -433,7 +424,7 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
       d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
-      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.erep, p.d_twiddle, p.d_part, p.d_part_auto)
+      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
   } else {
@@ -449,7 +440,7 @@ cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, co
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
       d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
-      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.erep, p.d_twiddle, part, part_auto)
+      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, part, part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
   } else {

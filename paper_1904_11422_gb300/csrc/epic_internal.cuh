@@ -63,7 +63,7 @@ struct Plan {
   GatherTables gt;              // gridder's lane-interleaved gather tables
 
   // imaging launch shape and its workspace (partial images per CTA span)
-  int ctas = 0, threads = 0, spans = 0, ent_in_smem = 0, erep = 1;  // erep: copies of each field in smem
+  int ctas = 0, threads = 0, spans = 0, ent_in_smem = 0;
   size_t smem = 0;
   float* d_part = nullptr;      // [ctas][spans][4][N][N]
   int* d_part_auto = nullptr;   // [ctas][spans][A][4] exact integer self powers
