@@ -288,19 +288,19 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
         const int K = cnt_s[warp * 8 + n2];
         const int b = base_s[warp * 8 + n2] + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
-        for (int k = 0; k < K; ++k) {
-          const int a = ent_a[b + 32 * k];
-          const float w = ent_w[b + 32 * k];
+        for (int k = 0; k < K; k += 2) {  // K is even: two entries per step, added in order
+          const int a0 = ent_a[b + 32 * k], a1 = ent_a[b + 32 * k + 32];
+          const float w0 = ent_w[b + 32 * k], w1 = ent_w[b + 32 * k + 32];
           if constexpr (P == 2) {
-            const float4 ev = E4[a];
-            gx.x = fmaf(w, ev.x, gx.x);
-            gx.y = fmaf(w, ev.y, gx.y);
-            gy.x = fmaf(w, ev.z, gy.x);
-            gy.y = fmaf(w, ev.w, gy.y);
+            const float4 e0 = E4[a0], e1 = E4[a1];
+            gx.x = fmaf(w1, e1.x, fmaf(w0, e0.x, gx.x));
+            gx.y = fmaf(w1, e1.y, fmaf(w0, e0.y, gx.y));
+            gy.x = fmaf(w1, e1.z, fmaf(w0, e0.z, gy.x));
+            gy.y = fmaf(w1, e1.w, fmaf(w0, e0.w, gy.y));
           } else {
-            const float2 ev = E2[a];
-            gx.x = fmaf(w, ev.x, gx.x);
-            gx.y = fmaf(w, ev.y, gx.y);
+            const float2 e0 = E2[a0], e1 = E2[a1];
+            gx.x = fmaf(w1, e1.x, fmaf(w0, e0.x, gx.x));
+            gx.y = fmaf(w1, e1.y, fmaf(w0, e0.y, gx.y));
           }
         }
         v[0][n2] = gx;

@@ -5,7 +5,9 @@
 // by build_csr_kernel, antenna order).  An imaging kernel thread owns 8 cells
 // ("slots"); the 32 threads of a warp walk their k-th entries in lock step.
 // This file lays those entries out for that walk: for warp w and slot s the
-// trip count K_ws is the largest cell count among the warp's 32 cells, and entry
+// trip count K_ws is the largest cell count among the warp's 32 cells (rounded
+// up to even for the FFT kernel, which walks entries two at a time to keep two
+// independent load chains in flight), and entry
 // k of lane l sits at base_ws + 32 k + l, cells with fewer entries padded with
 // weight-0 entries of antenna 0 (adding +0 leaves every sum unchanged, and the
 // real entries keep their antenna order, so the results are the same as a
@@ -103,7 +105,9 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
     const int2 yx = cells[s];
     beg[s] = ptr[yx.x * N + yx.y];
     cnt[s] = ptr[yx.x * N + yx.y + 1] - beg[s];
-    const int k = __reduce_max_sync(0xffffffffu, cnt[s]);
+    // FFT layouts: trip count rounded up to even (that kernel walks entries in pairs)
+    const int kmax = __reduce_max_sync(0xffffffffu, cnt[s]);
+    const int k = (layout == kLayoutFft64 || layout == kLayoutFft32) ? ((kmax + 1) & ~1) : kmax;
     if (lane == 0) kws[w * 8 + s] = k;
   }
   __syncthreads();
