@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="epic", choices=["epic", "reference"])
-    ap.add_argument("--xform", default="fft_fp32")
+    ap.add_argument("--xform", default="fft_fp32",
+                    help="primary transform (the JSON value); see --paths for the others timed")
+    ap.add_argument("--paths", default="dft_bf16x3,dft_fp16",
+                    help="further transforms timed the same way and reported under 'paths' ('' for none)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -63,6 +66,18 @@ def fp32_flops_per_tc(A, P, N, S):
     fft = P * 5 * N * N * int(math.log2(N * N))  # 5 N^2 log2(N^2) per 2-D FFT
     prod = N * N * (4 if P == 1 else 16)         # |X|^2, |Y|^2, X conj(Y), accumulated
     return calib + grid + fft + prod
+
+
+# Error bound stated for each transform, relative to the channel's image peak
+# (checked against the FP64 oracle by the parity tests).
+ERROR_BOUND = {"fft_fp32": 1e-5, "dft_bf16x3": 1e-3, "dft_fp16x3": 1e-3, "dft_fp16": 5e-3, "dft_bf16": 2e-2}
+
+
+def tensor_flops_per_tc(xform):
+    """Issued tensor-core flops of one (time, channel) image set: two stages of an
+    M = N = K = 128 real GEMM, times 3 for the hi+lo transforms."""
+    products = 3 if xform.endswith("x3") else 1
+    return products * 2 * (2 * 128 * 128 * 128)
 
 
 def peaks():
@@ -222,7 +237,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_1904_11422_gb300 import build_lib, epic, synth
+    from paper_1904_11422_gb300 import build_lib, epic, shard, synth
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -238,76 +253,89 @@ def main():
         dist.barrier()
 
     w = synth.station()
-    xform = epic.XFORMS[args.xform]
-    plan = epic.plan_for(w, xform, subtract_autos=True)
     T = w.n_time
     copies = [torch.from_numpy(w.volts).cuda() for _ in range(N_COPIES)]
-    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-
-    def step(i):
-        epic.epic_image(plan, copies[i % N_COPIES], T, out, 0, stream)
-
-    for i in range(max(3, args.warmup)):
-        step(i)
-    torch.cuda.synchronize()
-    epic.epic_sync(plan)
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    t_soak = time.perf_counter()
-    i = 0
-    while time.perf_counter() - t_soak < args.soak_seconds:  # untimed load, for the clock record
-        step(i)
-        i += 1
-        if i % 50 == 0:
-            torch.cuda.synchronize()
-    torch.cuda.synchronize()
 
-    epic.epic_timing_enable(plan, True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for i in range(args.steps):
-        step(i)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    kt = epic.epic_timing_read(plan)
-    epic.epic_timing_enable(plan, False)
-    clocks = sampler.stop()
-    epic.epic_sync(plan)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def time_path(xf, soak):
+        plan = epic.plan_for(w, epic.XFORMS[xf], subtract_autos=True)
+        out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
 
-    units_step = w.units
-    value = units_step * args.steps * world / (ms / 1e3)
+        def step(i):
+            epic.epic_image(plan, copies[i % N_COPIES], T, out, 0, stream)
 
-    # roofline of the dominant kernel
-    pk, pk_kind = peaks()
-    launches = sum(v[0] for v in kt.values())
-    dom = max(kt.items(), key=lambda kv: kv[1][1])[0] if kt else None
-    roof = None
-    if dom == "fft_image":
+        for i in range(max(3, args.warmup)):
+            step(i)
+        torch.cuda.synchronize()
+        epic.epic_sync(plan)
+        t_soak = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t_soak < soak:  # untimed load, for the clock record
+            step(i)
+            i += 1
+            if i % 50 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        epic.epic_timing_enable(plan, True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        kt = epic.epic_timing_read(plan)
+        epic.epic_timing_enable(plan, False)
+        epic.epic_sync(plan)
+        ms = shard.max_over_ranks(ms, device="cuda")
+        value = w.units * args.steps * world / (ms / 1e3)
+        launches = sum(v[0] for v in kt.values())
+        dom = max(kt.items(), key=lambda kv: kv[1][1])[0]
         n, tot = kt[dom]
         avg_s = tot / n / 1e3
-        flops = w.n_chan * T * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
-        sms = torch.cuda.get_device_properties(0).multi_processor_count
-        peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = flops / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": dram_traffic("fft_image", "epic_fft.cu"),
-                "kernel": "fft_image", "kernel_ms": 1e3 * avg_s, "kernel_share": tot / sum(v[1] for v in kt.values()),
-                "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
-                              f"(max SM clock, {pk_kind})",
-                "flops_per_launch": flops}
+        share = tot / sum(v[1] for v in kt.values())
+        if dom == "fft_image":
+            flops = w.n_chan * T * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
+            peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "traffic": dram_traffic("fft_image", "epic_fft.cu"), "kernel": dom,
+                    "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
+                                  f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz (max SM clock, {pk_kind})"}
+        else:
+            flops = w.n_chan * T * tensor_flops_per_tc(xf)
+            peak = pk.get("bf16_tflops", 1900.0)
+            roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "traffic": dram_traffic("dft_image", "epic_dft.cu"), "kernel": dom,
+                    "peak_basis": f"measured dense BF16 cuBLAS burst ({pk_kind}); FP16 dense rate taken equal",
+                    "useful_tflops": flops / (3 if xf.endswith("x3") else 1) / avg_s / 1e12}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof.update({"kernel_ms": 1e3 * avg_s, "kernel_share": share, "flops_per_launch": flops})
+        res = {"value": value, "ms_per_step": ms / args.steps, "roofline": roof, "gpu_launches": launches,
+               "error_bound": ERROR_BOUND.get(xf), "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]}
+                                                                       for k, v in kt.items()}}
+        return plan, res
+
+    plan, primary = time_path(args.xform, args.soak_seconds)
+    others = {}
+    for xf in [x for x in args.paths.split(",") if x and x != args.xform]:
+        p2, r2 = time_path(xf, 0.0)
+        p2.close()
+        others[xf] = r2
+    clocks = sampler.stop()
+    units_step = w.units
+    value = primary["value"]
+    ms = primary["ms_per_step"] * args.steps
 
     # end to end through the public host-buffer entry point
     e2e = None
@@ -323,10 +351,7 @@ def main():
         for _ in range(args.e2e_steps):
             epic.epic_image_host(plan, h_in, T, h_out, 0, stream)
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = shard.max_over_ranks(dt, device="cuda")
         e2e = {"value": units_step * args.e2e_steps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(w.volts.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 4),
                "steps": args.e2e_steps, "api": "epic_image_host (pinned host buffers, synchronous)"}
@@ -344,12 +369,13 @@ def main():
                 "dtype": "f32" if args.xform == "fft_fp32" else args.xform,
                 "data": "synthetic (seeded, LWA-station-shaped; no LWA-SV captures exist here)",
                 "config": {"workload": WORKLOAD, "xform": args.xform, "units_per_step": units_step,
+                           "error_bound": ERROR_BOUND.get(args.xform),
                            "parallelism": f"channel-independent blocks, one per GPU x {world}",
                            "l2": f"inputs larger than L2: {N_COPIES} rotating device copies of the block "
                                  f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kt.items()},
-                "clocks": clocks}
+                "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": primary["gpu_launches"], "kernel_times_ms": primary["kernel_times_ms"],
+                "paths": others, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

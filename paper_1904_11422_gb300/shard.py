@@ -1,0 +1,44 @@
+"""Channel sharding across ranks (one GPU per rank).
+
+Channels are imaged independently (Sec. 5: each GPU of the deployment takes its
+own slice of the band), so a multi-GPU run splits the channels into contiguous,
+balanced ranges with no data-path collective.  Collectives appear only off the
+hot path: assembling the full image set on one rank, and the max-over-ranks
+timing of a benchmark.
+"""
+from __future__ import annotations
+
+
+def channel_shard(n_chan: int, rank: int, world: int) -> tuple[int, int]:
+    """[c_lo, c_hi) of rank's channels: contiguous, sizes differing by at most 1."""
+    if world < 1 or not 0 <= rank < world or n_chan < 0:
+        raise ValueError("bad shard request")
+    base, extra = divmod(n_chan, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def gather_channels(local, n_chan: int, group=None):
+    """All ranks' [c_hi-c_lo][...] image blocks concatenated in channel order
+    (every rank receives the full [n_chan][...] tensor).  Off the hot path."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    sizes = [channel_shard(n_chan, r, world) for r in range(world)]
+    width = max(hi - lo for lo, hi in sizes)
+    pad = torch.zeros((width,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
+    pad[: local.shape[0]] = local
+    parts = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(parts, pad, group=group)
+    return torch.cat([parts[r][: hi - lo] for r, (lo, hi) in enumerate(sizes)], dim=0)
+
+
+def max_over_ranks(x: float, device=None, group=None) -> float:
+    """The largest value of x over all ranks (timing: the slowest rank decides)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
