@@ -82,6 +82,8 @@ def _load():
             lib.eo_fx_gridded.argtypes = [A, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
             lib.eo_fx_gridded.restype = ctypes.c_int
             lib.eo_max_threads.restype = ctypes.c_int
+            lib.eo_grad_fx.argtypes = [A, _U8, ctypes.c_int, _D, _D, _D]
+            lib.eo_grad_fx.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -275,3 +277,25 @@ def fx_gridded(arr: OracleArray, volts, c: int, include_autos: bool) -> np.ndarr
 def pixel_lm(N: int, cell_lambda: float, i: int, j: int) -> tuple[float, float]:
     """Reading R4: direction cosines of pixel (i, j) (column i, row j)."""
     return (i - N / 2) / (N * cell_lambda), (j - N / 2) / (N * cell_lambda)
+
+
+def grad_fx(arr: OracleArray, volts, model):
+    """Gradient of L = sum (I - M)^2 over XX, YY and all pixels and channels with
+    respect to the complex gains, closed form from the FX image (small cases).
+    Returns (loss, grad) with grad [C][A][P] complex = dL/dRe g + i dL/dIm g."""
+    v, T = _volts(arr, volts)
+    m = np.ascontiguousarray(model, np.float64).reshape(arr.n_chan, 2, arr.grid_n, arr.grid_n)
+    g = np.zeros((arr.n_chan, arr.n_ant, arr.n_pol, 2), np.float64)
+    loss = ctypes.c_double()
+    rc = _load().eo_grad_fx(arr.ref, v.ctypes.data_as(_U8), T, _dptr(m), _dptr(g), ctypes.byref(loss))
+    if rc != 0:
+        raise ValueError("antenna box leaves the grid")
+    return loss.value, g[..., 0] + 1j * g[..., 1]
+
+
+def loss_epic(arr: OracleArray, volts, model) -> float:
+    """L = sum over channels, XX and YY, pixels of (I - M)^2 with I from eo_image."""
+    img = image(arr, volts, subtract=True)
+    m = np.asarray(model, np.float64).reshape(arr.n_chan, 2, arr.grid_n, arr.grid_n)
+    planes = [0] if arr.n_pol == 1 else [0, 1]
+    return float(sum(np.sum((img[:, p] - m[:, p]) ** 2) for p in planes))

@@ -17,7 +17,7 @@
  *            lambda/2 grid with a user-defined illumination kernel, inverse
  *            spatial FT, square / cross-multiply, accumulate, remove autos.
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   R1 sample byte: real part in the high nibble, imaginary part in the low
  *      nibble, both 4-bit two's complement in [-8, 7].
  *   R3 transform: exp(+2 pi i (...)) as printed in Eq. (5), unnormalised.
@@ -561,4 +561,97 @@ int eo_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the image-plane calibration loss with respect to the complex  */
+/* gains (the gain multiplication of Fig. 2, solved for by the EPICal block  */
+/* the paper plans in Sec. 6):                                               */
+/*   L = sum_c sum_{pp in XX, YY} sum_pix (I_pp - M_pp)^2,                   */
+/* with I the autocorrelation-removed image.  From the FX form (Eq. (2)),    */
+/*   I_pp = sum_{a != b} g_ap conj(g_bp) V~_ab W_a conj(W_b),                */
+/* V~_ab = sum_t e~_a conj(e~_b) the visibilities without gains (e~ carries  */
+/* the delay phase only), W_a the FT of antenna a's placed kernel.  Hence    */
+/*   dL/d conj(g_cp) = sum_pix R_pp sum_{a != c} g_ap V~_ac W_a conj(W_c),   */
+/* R = 2 (I - M), and the gradient in the convention dL/dRe g + i dL/dIm g   */
+/* is twice that.  model is [C][2][N][N] (XX, YY); grad [C][A][P][2]; loss a */
+/* scalar.  O(A^2 N^2) per channel and polarisation: small cases only.       */
+/* ------------------------------------------------------------------------ */
+int eo_grad_fx(const eo_array* d, const uint8_t* volts, int T, const double* model, double* grad, double* loss) {
+  const int N = d->grid_n, A = d->n_ant, P = d->n_pol, C = d->n_chan, NN = N * N;
+  if (A > 1024) return -2;
+  eo_array dn = *d;
+  dn.gains = NULL;  /* visibilities without gains: delay phase only */
+  double* v = (double*)malloc(sizeof(double) * 3 * A * A * 2);
+  double* wr = (double*)malloc(sizeof(double) * (int64_t)A * NN);
+  double* wi = (double*)malloc(sizeof(double) * (int64_t)A * NN);
+  double* img = (double*)malloc(sizeof(double) * NN);
+  double total = 0.0;
+  memset(grad, 0, sizeof(double) * (size_t)C * A * P * 2);
+  for (int c = 0; c < C; ++c) {
+    for (int a = 0; a < A; ++a)
+      if (eo_antenna_kernel(d, c, a, NULL, NULL, NULL, NULL, NULL) != 0) {
+        free(v); free(wr); free(wi); free(img);
+        return -1;
+      }
+    eo_visibilities(&dn, volts, T, c, v);
+    for (int a = 0; a < A; ++a) eo_kernel_ft(d, c, a, wr + (int64_t)a * NN, wi + (int64_t)a * NN);
+    for (int p = 0; p < P; ++p) {
+      const int pq = p;  /* XX for p = 0, YY for p = 1 */
+      double gr[1024], gi[1024];
+      for (int a = 0; a < A && a < 1024; ++a) {
+        gr[a] = 1.0; gi[a] = 0.0;
+        if (d->gains) {
+          gr[a] = d->gains[2 * (((int64_t)c * A + a) * P + p)];
+          gi[a] = d->gains[2 * (((int64_t)c * A + a) * P + p) + 1];
+        }
+      }
+      /* I_pp over the pixels */
+      for (int k = 0; k < NN; ++k) {
+        double s = 0.0;
+        for (int a = 0; a < A; ++a)
+          for (int b = 0; b < A; ++b) {
+            if (a == b) continue;
+            const double* vv = v + 2 * (((int64_t)pq * A + a) * A + b);
+            /* g_a conj(g_b) */
+            const double qr = gr[a] * gr[b] + gi[a] * gi[b], qi = gi[a] * gr[b] - gr[a] * gi[b];
+            /* W_a conj(W_b) */
+            const double ar = wr[(int64_t)a * NN + k], ai = wi[(int64_t)a * NN + k];
+            const double br = wr[(int64_t)b * NN + k], bi = -wi[(int64_t)b * NN + k];
+            const double mr = ar * br - ai * bi, mi = ar * bi + ai * br;
+            const double tr = qr * vv[0] - qi * vv[1], ti = qr * vv[1] + qi * vv[0];
+            s += tr * mr - ti * mi;  /* real part; the imaginary parts cancel over (a, b), (b, a) */
+          }
+        img[k] = s;
+      }
+      const double* M = model + ((int64_t)c * 2 + pq) * NN;
+      for (int k = 0; k < NN; ++k) total += (img[k] - M[k]) * (img[k] - M[k]);
+      /* gradient */
+      for (int cc = 0; cc < A; ++cc) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < NN; ++k) {
+          const double R = 2.0 * (img[k] - M[k]);
+          double ur = 0.0, ui = 0.0;  /* sum_{a != cc} g_a V~_{a cc} W_a */
+          for (int a = 0; a < A; ++a) {
+            if (a == cc) continue;
+            const double* vv = v + 2 * (((int64_t)pq * A + a) * A + cc);
+            const double tr = gr[a] * vv[0] - gi[a] * vv[1], ti = gr[a] * vv[1] + gi[a] * vv[0];
+            const double ar = wr[(int64_t)a * NN + k], ai = wi[(int64_t)a * NN + k];
+            ur += tr * ar - ti * ai;
+            ui += tr * ai + ti * ar;
+          }
+          /* times conj(W_cc) */
+          const double cr = wr[(int64_t)cc * NN + k], ci = -wi[(int64_t)cc * NN + k];
+          sr += R * (ur * cr - ui * ci);
+          si += R * (ur * ci + ui * cr);
+        }
+        double* o = grad + 2 * (((int64_t)c * A + cc) * P + p);
+        o[0] = 2.0 * sr;
+        o[1] = 2.0 * si;
+      }
+    }
+  }
+  *loss = total;
+  free(v); free(wr); free(wi); free(img);
+  return 0;
 }

@@ -360,3 +360,42 @@ def test_planted_mistakes_are_caught(oracle_lib, name):
 def test_pins_pass_without_mutation(oracle_lib):
     res = _pins_pass()
     assert all(res.values()), res
+
+
+# --------------------------------------------------------------------------
+# Gain gradient of the image-plane loss: FX closed form against central
+# finite differences of the EPIC-form image (two independent computations)
+# --------------------------------------------------------------------------
+def _grad_case(seed, **kw):
+    w = synth.random_small(seed, **kw)
+    arr = _arr(w)
+    rng = np.random.default_rng(seed + 1000)
+    model = rng.standard_normal((w.n_chan, 2, w.grid_n, w.grid_n)) * 50.0
+    return w, arr, model
+
+
+@pytest.mark.parametrize("seed,kw", [
+    (1201, dict(n_ant=5, n_pol=2, n_chan=2, grid_n=16, support=3, n_time=4)),
+    (1202, dict(n_ant=4, n_pol=1, n_chan=1, grid_n=16, support=5, n_time=6)),
+    (1203, dict(n_ant=6, n_pol=2, n_chan=1, grid_n=8, support=1, n_time=3)),
+])
+def test_gradient_fx_closed_form_matches_finite_differences(oracle_lib, seed, kw):
+    w, arr, model = _grad_case(seed, **kw)
+    loss, grad = oracle.grad_fx(arr, w.volts, model)
+    assert loss == pytest.approx(oracle.loss_epic(arr, w.volts, model), rel=1e-10)
+    rng = np.random.default_rng(seed)
+    h = 1e-4
+    idx = [tuple(int(x) for x in (rng.integers(w.n_chan), rng.integers(w.n_ant), rng.integers(w.n_pol)))
+           for _ in range(12)]
+    scale = np.abs(grad).max()
+    for (c, a, p) in idx:
+        fd = 0j
+        for unit in (1.0, 1j):
+            gp = w.gains.copy()
+            gm = w.gains.copy()
+            gp[c, a, p] += h * unit
+            gm[c, a, p] -= h * unit
+            lp = oracle.loss_epic(_arr(w, gains=gp), w.volts, model)
+            lm = oracle.loss_epic(_arr(w, gains=gm), w.volts, model)
+            fd += unit * (lp - lm) / (2 * h)
+        assert abs(fd - grad[c, a, p]) <= 1e-6 * scale, (c, a, p, fd, grad[c, a, p])
