@@ -177,6 +177,28 @@ epic_status epic_image_host(epic_plan* plan, const uint8_t* h_volts, int n_time,
 epic_status epic_image_noalloc(epic_plan* plan, const uint8_t* d_volts, int n_time, float* d_out,
                                int accumulate, void* stream);
 
+/* Gradient of an image-plane calibration loss with respect to the complex
+ * per-antenna gains, for real-time gain calibration (the gain multiplication of
+ * Fig. 2, solved for by the EPICal block the paper plans in Sec. 6):
+ *     L = sum_c sum_{pp in XX, YY} sum_pix (I_pp(pix) - M_pp(pix))^2
+ * where I is the plan's image of the block (autocorrelations removed when the
+ * plan removes them) computed with calibration coefficients
+ * k = g exp(-2 pi i nu tau): g from d_gains, tau the plan's delays (the plan's
+ * own gains are not used).
+ *   d_volts  device [n_time][n_chan][n_ant][n_pol] bytes as in epic_image, n_time >= 1
+ *   d_gains  device [n_chan][n_ant][n_pol][2] float (re, im)
+ *   d_model  device [n_chan][2][N][N] float: M_XX, M_YY (M_YY unused for one pol)
+ *   d_grad   device [n_chan][n_ant][n_pol][2] float: dL/dRe g, dL/dIm g
+ *            (= 2 dL/d conj(g))
+ *   d_loss   device float: L
+ * The gridded fields are recomputed in a second pass over the block rather than
+ * stored (forward image, residual R = 2 (I - M), then per sample the conjugate
+ * transform of R . Y degridded onto each antenna).  FP32 FFT plans with N = 64
+ * and at most 512 antennas; others return EPIC_ERR_UNSUPPORTED.  Uses the
+ * plan's workspace; asynchronous. */
+epic_status epic_grad(epic_plan* plan, const uint8_t* d_volts, int n_time, const float* d_gains,
+                      const float* d_model, float* d_grad, float* d_loss, void* stream);
+
 /* Waits for the stream and reports any device-side error recorded by the
  * plan's kernels since the previous call (EPIC_ERR_TIMEOUT, EPIC_ERR_CUDA). */
 epic_status epic_sync(epic_plan* plan, void* stream);

@@ -60,7 +60,8 @@ void free_plan(Plan& p) {
   p.event_pool.clear();
   void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
                   p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
-                  p.d_stage_in, p.d_stage_out, p.d_fmat};
+                  p.d_stage_in, p.d_stage_out, p.d_fmat, p.d_dphase, p.d_gcoef, p.d_gcoef64, p.d_gimage,
+                  p.d_resid, p.d_loss_part, p.d_gpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   epic::free_gather_tables(p.gt);
@@ -230,6 +231,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   EPIC_TRY(alloc(&p.d_wy, C * A * S, &total));
   EPIC_TRY(alloc(&p.d_coef, C * A * P, &total));
   EPIC_TRY(alloc(&p.d_coef64, C * A * P, &total));
+  EPIC_TRY(alloc(&p.d_dphase, C * A * P, &total));
   EPIC_TRY(alloc(&p.d_kx2, C * A * N, &total));
   EPIC_TRY(alloc(&p.d_ky2, C * A * N, &total));
   EPIC_TRY(alloc(&p.d_csr_ptr, C * (N * N + 1), &total));
@@ -287,6 +289,17 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * N * N, &total));
   EPIC_TRY(alloc(&p.d_part_auto, (size_t)p.ctas * p.spans * A * 4, &total));
   p.workspace_bytes = total - before;
+  // epic_grad: FP32 FFT plans of 64 x 64 grids with one antenna per thread
+  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 64 && p.A <= 512 && epic::adjoint_smem_need(p) <= kSmemOptin) {
+    EPIC_TRY(alloc(&p.d_gcoef, C * A * P, &total));
+    EPIC_TRY(alloc(&p.d_gcoef64, C * A * P, &total));
+    EPIC_TRY(alloc(&p.d_gimage, C * 4 * N * N, &total));
+    EPIC_TRY(alloc(&p.d_resid, C * 2 * N * N, &total));
+    EPIC_TRY(alloc(&p.d_loss_part, C, &total));
+    EPIC_TRY(alloc(&p.d_gpart, (size_t)p.ctas * p.spans * A * P, &total));
+    EPIC_TRY(cudaMemset(p.d_resid, 0, sizeof(float) * C * 2 * N * N));
+    p.grad_ok = true;
+  }
   p.device_bytes = total;
 #undef EPIC_TRY
   *out = h;
@@ -376,6 +389,25 @@ epic_status epic_sync(epic_plan* h, void* stream) {
   if (status == epic::kDevOk) return EPIC_OK;
   cudaMemset(h->p.d_status, 0, sizeof(int));
   return status == epic::kDevTimeout ? EPIC_ERR_TIMEOUT : EPIC_ERR_CUDA;
+}
+
+epic_status epic_grad(epic_plan* h, const uint8_t* d_volts, int n_time, const float* d_gains,
+                      const float* d_model, float* d_grad, float* d_loss, void* stream) {
+  if (!h || !d_volts || !d_gains || !d_model || !d_grad || !d_loss || n_time < 1 || n_time > (1 << 24))
+    return EPIC_ERR_INVALID_ARG;
+  Plan& p = h->p;
+  if (!p.grad_ok) return EPIC_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const epic::WorkSplit ws = split_work(p, n_time);
+  cudaError_t e = epic::launch_grad_coef(p, d_gains, s);
+  if (e == cudaSuccess)
+    e = timed(p, "fft_image", s, [&] { return epic::launch_fft_image_coef(p, d_volts, n_time, ws, p.d_gcoef, s); });
+  if (e == cudaSuccess)
+    e = timed(p, "reduce", s, [&] { return epic::launch_reduce_coef(p, n_time, ws, p.d_gcoef64, p.d_gimage, s); });
+  if (e == cudaSuccess) e = epic::launch_residual(p, d_model, d_loss, s);
+  if (e == cudaSuccess) e = timed(p, "adjoint", s, [&] { return epic::launch_adjoint(p, d_volts, n_time, ws, s); });
+  if (e == cudaSuccess) e = epic::launch_grad_reduce(p, n_time, ws, d_gains, d_grad, s);
+  return from_cuda(e);
 }
 
 epic_status epic_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, void* stream) {

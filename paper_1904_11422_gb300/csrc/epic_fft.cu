@@ -468,4 +468,332 @@ cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint pass of the gain gradient (epic_grad), N = 64.
+//
+// For L = sum_pix (I_pp - M_pp)^2 with R = 2 (I - M), the gradient with respect
+// to conj(g_ap) has a data term
+//   sum_t conj(e~_ap(t)) D_ap(t),  D_ap(t) = sum_cells w_a(cell) H_p,t(cell),
+//   H_p,t = F^H (R_pp . Y_p,t)   (the transform of Eq. (5) with the opposite sign)
+// where e~ is the delay-compensated field without the gain and Y the image of
+// sample t.  The gridded fields are recomputed per sample, not stored: each
+// unit repeats the forward gather + FFT of fft_image_kernel, multiplies by R,
+// runs the conjugate FFT (conj, the same +i line transforms, conj) through the
+// same register layouts in reverse (columns, then rows), and degrids H over each
+// antenna's kernel box.  Per-antenna sums stay in registers (thread a owns
+// antenna a) and are written per channel span, like the partial images.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjSmem {
+  size_t R, scr, wst, coef, dph, E, resid, box, wts, ent_a, ent_w, total;
+};
+
+template <int P>
+__host__ __device__ inline AdjSmem adj_smem_layout(int A, int S, int max_entries, int ent_in_smem) {
+  using G = Geo<64>;
+  AdjSmem L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 15) & ~(size_t)15;
+    return at;
+  };
+  L.R = take(sizeof(float2) * P * 64 * 64);
+  L.scr = take(sizeof(float2) * (G::THREADS / 32) * G::SCR);
+  L.wst = take(sizeof(int) * 2 * (G::THREADS / 32) * 8);
+  L.coef = take(sizeof(float2) * A * P);
+  L.dph = take(sizeof(float2) * A * P);
+  L.E = take((P == 2 ? 16 : 8) * (size_t)(A + 1));
+  L.resid = take(sizeof(float) * P * 64 * 64);
+  L.box = take(sizeof(int2) * A);
+  L.wts = take(sizeof(float) * 2 * (size_t)A * S);
+  L.ent_a = take(ent_in_smem ? sizeof(uint16_t) * (size_t)max_entries : 0);
+  L.ent_w = take(ent_in_smem ? sizeof(float) * (size_t)max_entries : 0);
+  L.total = o;
+  return L;
+}
+
+template <int P>
+__global__ void __launch_bounds__(512, 1)
+    adjoint_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, int S, long long W, long long units,
+                   int spans, const float2* __restrict__ coef, const double2* __restrict__ dphase,
+                   const int* __restrict__ g_cnt, const int* __restrict__ g_base, const int* __restrict__ g_off,
+                   const uint16_t* __restrict__ g_ent_a, const float* __restrict__ g_ent_w, int max_entries,
+                   int ent_in_smem, const float2* __restrict__ twiddle, const float* __restrict__ resid,
+                   const int* __restrict__ box, const double* __restrict__ wx, const double* __restrict__ wy,
+                   float2* __restrict__ gpart) {
+  using G = Geo<64>;
+  constexpr int N = 64, NT = 512, NN = N * N, R1 = 8, HALF = 32, WARPS = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const AdjSmem L = adj_smem_layout<P>(A, S, max_entries, ent_in_smem);
+  float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
+  float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
+  int* cnt_s = reinterpret_cast<int*>(smem + L.wst);
+  int* base_s = cnt_s + WARPS * 8;
+  float2* coef_s = reinterpret_cast<float2*>(smem + L.coef);
+  float2* dph_s = reinterpret_cast<float2*>(smem + L.dph);
+  float4* E4 = reinterpret_cast<float4*>(smem + L.E);
+  float2* E2 = reinterpret_cast<float2*>(smem + L.E);
+  float* res_s = reinterpret_cast<float*>(smem + L.resid);
+  int2* box_s = reinterpret_cast<int2*>(smem + L.box);
+  float* wx_s = reinterpret_cast<float*>(smem + L.wts);
+  float* wy_s = wx_s + (size_t)A * S;
+  uint16_t* enta_s = reinterpret_cast<uint16_t*>(smem + L.ent_a);
+  float* entw_s = reinterpret_cast<float*>(smem + L.ent_w);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int line = tid / R1, n1 = tid % R1, r = line % G::RPW;
+  float2 tw[8];
+  tw[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[(n1 * k2) & (N - 1)];
+
+  const long long u0 = (long long)blockIdx.x * W;
+  const long long u1 = min(u0 + W, units);
+  if (u0 >= u1) return;
+  const int c_first = (int)(u0 / T);
+
+  float2 gacc[P];  // thread a (< A): sum_t conj(e~) D of its antenna
+#pragma unroll
+  for (int p = 0; p < P; ++p) gacc[p] = make_float2(0.f, 0.f);
+  const uint16_t* ent_a = g_ent_a;
+  const float* ent_w = g_ent_w;
+  int cur_c = -1;
+
+  auto flush = [&](int c) {
+    if (tid < A) {
+      float2* dst = gpart + ((size_t)((long long)blockIdx.x * spans + (c - c_first)) * A + tid) * P;
+#pragma unroll
+      for (int p = 0; p < P; ++p) dst[p] = gacc[p];
+    }
+  };
+
+  for (long long u = u0; u < u1; ++u) {
+    const int c = (int)(u / T), t = (int)(u % T);
+    if (c != cur_c) {
+      if (cur_c >= 0) {
+        flush(cur_c);
+#pragma unroll
+        for (int p = 0; p < P; ++p) gacc[p] = make_float2(0.f, 0.f);
+      }
+      cur_c = c;
+      __syncthreads();  // the previous unit's degrid has finished with the tables
+      if (tid < WARPS * 8) {
+        cnt_s[tid] = g_cnt[(size_t)c * WARPS * 8 + tid];
+        base_s[tid] = g_base[(size_t)c * WARPS * 8 + tid];
+      }
+      for (int k = tid; k < A * P; k += NT) {
+        coef_s[k] = coef[(size_t)c * A * P + k];
+        const double2 d = dphase[(size_t)c * A * P + k];
+        dph_s[k] = make_float2((float)d.x, (float)d.y);
+      }
+      for (int k = tid; k < P * NN; k += NT) res_s[k] = resid[(size_t)c * 2 * NN + k];
+      for (int a = tid; a < A; a += NT) {
+        box_s[a] = make_int2(box[((size_t)c * A + a) * 2], box[((size_t)c * A + a) * 2 + 1]);
+        for (int k = 0; k < S; ++k) {
+          wx_s[a * S + k] = (float)wx[((size_t)c * A + a) * S + k];
+          wy_s[a * S + k] = (float)wy[((size_t)c * A + a) * S + k];
+        }
+      }
+      const int e0 = g_off[c], ne = g_off[c + 1] - e0;
+      if (ent_in_smem) {
+        for (int k = tid; k < ne; k += NT) {
+          enta_s[k] = g_ent_a[e0 + k];
+          entw_s[k] = g_ent_w[e0 + k];
+        }
+        ent_a = enta_s;
+        ent_w = entw_s;
+      } else {
+        ent_a = g_ent_a + e0;
+        ent_w = g_ent_w + e0;
+      }
+      __syncthreads();
+    }
+
+    // 1. unpack and calibrate with the call's coefficients (thread a = tid)
+    unsigned raw = 0;
+    if (tid < A) {
+      const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
+      if constexpr (P == 2)
+        raw = __ldg(reinterpret_cast<const unsigned short*>(base) + tid);
+      else
+        raw = __ldg(base + tid);
+      const int xr = nib_hi(raw & 0xffu), xi = nib_lo(raw & 0xffu);
+      const float2 kx = coef_s[tid * P];
+      const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
+      if constexpr (P == 2) {
+        const int yr = nib_hi(raw >> 8), yi = nib_lo(raw >> 8);
+        const float2 ky = coef_s[tid * P + 1];
+        E4[tid] = make_float4(ex.x, ex.y, ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
+      } else {
+        E2[tid] = ex;
+      }
+    }
+    __syncthreads();
+
+    // 2. forward: gather (same tables and order as the imaging kernel), row FFTs
+    {
+      const int y = line;
+      float2 v[P][8];
+#pragma unroll
+      for (int n2 = 0; n2 < 8; ++n2) {
+        const int K = cnt_s[warp * 8 + n2];
+        const int b = base_s[warp * 8 + n2] + lane;
+        float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
+        for (int k = 0; k < K; k += 2) {
+          const int a0 = ent_a[b + 32 * k], a1 = ent_a[b + 32 * k + 32];
+          const float w0 = ent_w[b + 32 * k], w1 = ent_w[b + 32 * k + 32];
+          if constexpr (P == 2) {
+            const float4 e0 = E4[a0], e1 = E4[a1];
+            gx.x = fmaf(w1, e1.x, fmaf(w0, e0.x, gx.x));
+            gx.y = fmaf(w1, e1.y, fmaf(w0, e0.y, gx.y));
+            gy.x = fmaf(w1, e1.z, fmaf(w0, e0.z, gy.x));
+            gy.y = fmaf(w1, e1.w, fmaf(w0, e0.w, gy.y));
+          } else {
+            const float2 e0 = E2[a0], e1 = E2[a1];
+            gx.x = fmaf(w1, e1.x, fmaf(w0, e0.x, gx.x));
+            gx.y = fmaf(w1, e1.y, fmaf(w0, e0.y, gx.y));
+          }
+        }
+        v[0][n2] = gx;
+        if constexpr (P == 2) v[1][n2] = gy;
+      }
+      const int sw = G::swz(y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        fft_line<N>(v[p], tw, scr, r, n1);
+        float2* Rrow = Rbuf + (size_t)p * NN + y * N;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) Rrow[G::kidx(n1, s) ^ sw] = v[p][s];
+      }
+    }
+    __syncthreads();
+
+    // 3. forward column FFTs -> Y; conj(R . Y); conjugate column FFTs; write back
+    {
+      const int k = line;
+      const int col = (k + HALF) & (N - 1);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        float2 v[8];
+#pragma unroll
+        for (int m2 = 0; m2 < 8; ++m2) {
+          const int y = n1 + R1 * m2;
+          v[m2] = Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))];
+        }
+        fft_line<N>(v, tw, scr, r, n1);
+        // thread (k, q = n1) holds Y[j = n1 + 8 s][k]; pixel row (j + N/2) mod N
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int row = (G::kidx(n1, s) + HALF) & (N - 1);
+          const float rr = res_s[(size_t)p * NN + row * N + col];
+          v[s] = make_float2(rr * v[s].x, -rr * v[s].y);  // conj(R Y)
+        }
+        fft_line<N>(v, tw, scr, r, n1);  // element index n1 + 8 s: the input layout again
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int y = G::kidx(n1, s);
+          Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))] = v[s];
+        }
+      }
+    }
+    __syncthreads();
+
+    // 4. conjugate row FFTs -> H = conj(result) on the thread's own cells (y, n1 + 8 s)
+    {
+      const int y = line;
+      const int sw = G::swz(y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        float2 v[8];
+        float2* Rrow = Rbuf + (size_t)p * NN + y * N;
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rrow[(n1 + R1 * n2) ^ sw];
+        fft_line<N>(v, tw, scr, r, n1);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) Rrow[G::kidx(n1, s) ^ sw] = make_float2(v[s].x, -v[s].y);
+      }
+    }
+    __syncthreads();
+
+    // 5. degrid H over each antenna's box and accumulate conj(e~) D
+    if (tid < A) {
+      const int2 bx = box_s[tid];
+      float2 D[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) D[p] = make_float2(0.f, 0.f);
+      for (int dy = 0; dy < S; ++dy) {
+        const int y = bx.y + dy;
+        const float wyv = wy_s[tid * S + dy];
+        const int sw = G::swz(y);
+        for (int dx = 0; dx < S; ++dx) {
+          const float w = wyv * wx_s[tid * S + dx];
+          const int idx = y * N + ((bx.x + dx) ^ sw);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const float2 h = Rbuf[(size_t)p * NN + idx];
+            D[p].x = fmaf(w, h.x, D[p].x);
+            D[p].y = fmaf(w, h.y, D[p].y);
+          }
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const unsigned b = (raw >> (8 * p)) & 0xffu;
+        const int re = nib_hi(b), im = nib_lo(b);
+        const float2 d = dph_s[tid * P + p];
+        const float er = d.x * re - d.y * im, ei = d.x * im + d.y * re;  // e~ = delay phase x E'
+        gacc[p].x = fmaf(er, D[p].x, fmaf(ei, D[p].y, gacc[p].x));     // conj(e~) D
+        gacc[p].y = fmaf(er, D[p].y, fmaf(-ei, D[p].x, gacc[p].y));
+      }
+    }
+  }
+  flush(cur_c);
+}
+
+}  // namespace
+
+cudaError_t launch_fft_image_coef(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, const float2* coef,
+                                  cudaStream_t s) {
+  const int ent = p.ent_in_smem;
+#define EPIC_LAUNCH(NN_, PP_)                                                                                   \
+  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
+      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,            \
+      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
+  if (p.N == 64) {
+    if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
+  } else {
+    if (p.P == 2) EPIC_LAUNCH(32, 2); else EPIC_LAUNCH(32, 1);
+  }
+#undef EPIC_LAUNCH
+  return cudaGetLastError();
+}
+
+namespace {
+size_t adj_smem(const Plan& p, int ent) {
+  return p.P == 2 ? adj_smem_layout<2>(p.A, p.S, p.gt.max_chan_entries, ent).total
+                  : adj_smem_layout<1>(p.A, p.S, p.gt.max_chan_entries, ent).total;
+}
+}  // namespace
+
+cudaError_t launch_adjoint(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int ent = adj_smem(p, 1) <= (size_t)optin ? 1 : 0;
+  const size_t smem = adj_smem(p, ent);
+  auto fn = p.P == 2 ? adjoint_kernel<2> : adjoint_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<ws.ctas, 512, smem, s>>>(d_volts, T, p.C, p.A, p.S, ws.W, ws.units, p.spans, p.d_gcoef, p.d_dphase,
+                                 p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off, p.gt.d_ent_a, p.gt.d_ent_w,
+                                 p.gt.max_chan_entries, ent, p.d_twiddle, p.d_resid, p.d_box, p.d_wx, p.d_wy,
+                                 p.d_gpart);
+  return cudaGetLastError();
+}
+
+size_t adjoint_smem_need(const Plan& p) { return adj_smem(p, 0); }
+
 }  // namespace epic

@@ -53,6 +53,7 @@ struct Plan {
   double* d_wy = nullptr;       // [C][A][S] along y
   float2* d_coef = nullptr;     // [C][A][P] calibration coefficient k (FP32)
   double2* d_coef64 = nullptr;  // [C][A][P] the same in FP64
+  double2* d_dphase = nullptr;  // [C][A][P] delay phase exp(-2 pi i nu tau) alone (FP64)
   float* d_kx2 = nullptr;       // [C][A][N] |FT of w_x|^2 per output column
   float* d_ky2 = nullptr;       // [C][A][N] |FT of w_y|^2 per output row
   int* d_csr_ptr = nullptr;     // [C][N*N+1] gather table: cell -> entries
@@ -81,6 +82,15 @@ struct Plan {
   std::vector<long long> kind_launches;
   std::vector<double> kind_ms;
 
+  // epic_grad workspace (FP32 FFT plans with N = 64 and A <= 512)
+  bool grad_ok = false;
+  float2* d_gcoef = nullptr;     // [C][A][P] coefficients g * delay phase of the call
+  double2* d_gcoef64 = nullptr;  // [C][A][P] the same in FP64
+  float* d_gimage = nullptr;     // [C][4][N][N] forward image of the call
+  float* d_resid = nullptr;      // [C][2][N][N] R = 2 (I - M) for XX, YY
+  double* d_loss_part = nullptr; // [C] per-channel loss
+  float2* d_gpart = nullptr;     // [ctas][spans][A][P] per-CTA sums of conj(e~) D
+
   // staging for epic_image_host
   uint8_t* d_stage_in = nullptr;
   size_t stage_in_bytes = 0;
@@ -107,6 +117,18 @@ cudaError_t launch_dft_tables(Plan& p, cudaStream_t s);
 cudaError_t dft_image_config(Plan& p, int* ctas_per_sm);
 cudaError_t launch_dft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                              int* part_auto, cudaStream_t s);
+
+// Gradient of the image-plane loss (epic_grad), FP32 FFT path at N = 64.
+cudaError_t launch_grad_coef(Plan& p, const float* d_gains, cudaStream_t s);
+cudaError_t launch_fft_image_coef(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, const float2* coef,
+                                  cudaStream_t s);
+cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double2* coef64, float* d_out,
+                               cudaStream_t s);
+cudaError_t launch_residual(Plan& p, const float* d_model, float* d_loss, cudaStream_t s);
+cudaError_t launch_adjoint(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s);
+cudaError_t launch_grad_reduce(Plan& p, int T, const WorkSplit& ws, const float* d_gains, float* d_grad,
+                               cudaStream_t s);
+size_t adjoint_smem_need(const Plan& p);
 
 // Block end: sum the CTA partials of every channel in a fixed order, remove the
 // autocorrelation term, write or accumulate the output.

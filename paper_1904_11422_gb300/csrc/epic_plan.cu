@@ -34,6 +34,7 @@ __global__ void plan_terms_kernel(int A, int P, int C, int N, int S, double cell
                                   const double* __restrict__ gains, const double* __restrict__ delays,
                                   int* __restrict__ box, double* __restrict__ wx, double* __restrict__ wy,
                                   float2* __restrict__ coef, double2* __restrict__ coef64,
+                                  double2* __restrict__ dphase,
                                   float* __restrict__ kx2, float* __restrict__ ky2, int* __restrict__ status) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)C * A) return;
@@ -100,6 +101,7 @@ __global__ void plan_terms_kernel(int A, int P, int C, int N, int S, double cell
     const double kr = gr * cs - gi * sn, ki = gr * sn + gi * cs;
     coef64[idx * P + p] = make_double2(kr, ki);
     coef[idx * P + p] = make_float2((float)kr, (float)ki);
+    dphase[idx * P + p] = make_double2(cs, sn);
   }
 }
 
@@ -178,7 +180,7 @@ cudaError_t launch_plan_terms(Plan& p, cudaStream_t s) {
   const long long blocks = (n + threads - 1) / threads;
   plan_terms_kernel<<<(unsigned)blocks, threads, 0, s>>>(p.A, p.P, p.C, p.N, p.S, p.cell_lambda, p.sigma,
                                                           p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box,
-                                                          p.d_wx, p.d_wy, p.d_coef, p.d_coef64, p.d_kx2, p.d_ky2,
+                                                          p.d_wx, p.d_wy, p.d_coef, p.d_coef64, p.d_dphase, p.d_kx2, p.d_ky2,
                                                           p.d_status);
   return cudaGetLastError();
 }

@@ -132,6 +132,22 @@ cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const fl
   return cudaGetLastError();
 }
 
+cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double2* coef64, float* d_out,
+                               cudaStream_t s) {
+  int rows = 1;
+  while (rows * p.N < kReduceThreads && rows < p.N) rows *= 2;
+  const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
+  auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(p.C, p.N / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, p.spans, p.subtract, 0, rows, p.d_part,
+                                        p.d_part_auto, coef64, p.d_kx2, p.d_ky2, d_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero(float* d_out, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const size_t blocks = (n + 255) / 256;

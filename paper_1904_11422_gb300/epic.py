@@ -75,6 +75,7 @@ SIGNATURES = {
     "epic_image_host": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_image_noalloc": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_sync": (_I, [_P, _P]),
+    "epic_grad": (_I, [_P, _P, _I, _P, _P, _P, _P, _P]),
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
@@ -252,6 +253,15 @@ EPIC_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 def epic_image_host(plan: Plan, h_volts, n_time: int, h_out, accumulate: int = 0, stream=None) -> None:
     _check(load_library().epic_image_host(plan.handle, _ptr(h_volts), int(n_time), _ptr(h_out),
                                           int(accumulate), _stream(stream)), "epic_image_host")
+
+
+def epic_grad(plan: Plan, d_volts, n_time: int, d_gains, d_model, d_grad, d_loss, stream=None) -> None:
+    """Loss and gain gradient of the image-plane calibration loss (see include/epic.h)."""
+    _check(load_library().epic_grad(plan.handle, _dev_tensor(d_volts, "uint8", "d_volts"), int(n_time),
+                                    _dev_tensor(d_gains, "float32", "d_gains"),
+                                    _dev_tensor(d_model, "float32", "d_model"),
+                                    _dev_tensor(d_grad, "float32", "d_grad"),
+                                    _dev_tensor(d_loss, "float32", "d_loss"), _stream(stream)), "epic_grad")
 
 
 def epic_sync(plan: Plan, stream=None) -> None:

@@ -208,3 +208,33 @@ def random_small(seed: int, n_ant: int = 6, n_pol: int = 2, n_chan: int = 2, gri
     sigma = max(support - 1, 1) / 4.0
     return Workload(f"random{seed}", ant, freq, n_pol, grid_n, support, 0.5, sigma, volts,
                     gains=gains, delays_s=delays)
+
+
+def differentiation(config_index: int = 4, n_chan: int = 64, n_time: int = 1250, n_sources: int = 5,
+                    noise_sigma: float = 2.5):
+    """Gain calibration on the station block: the station array, complex gains
+    with |g| uniform in 1 +- 0.1 and phase uniform in +- 0.3 rad (seed 4 + 100 x
+    config index), and voltages of the station recipe.  Also returns the voltages
+    of a noise-free sky of n_sources point sources on pixel centres (unit gains),
+    from which the model image is formed by whoever calls this.
+    Returns (workload with gains, noise-free sky workload)."""
+    w = station(config_index=1, n_time=n_time, n_chan=n_chan)
+    base = 100 * config_index
+    w.gains = random_gains(w.n_chan, w.n_ant, w.n_pol, 4 + base)
+    rng_s = np.random.default_rng(3 + base)
+    lm_amp, srcs = [], []
+    while len(srcs) < n_sources:
+        i, j = (int(x) for x in rng_s.integers(0, w.grid_n, size=2))
+        l, m = pixel_direction(w.grid_n, 0.5, i, j)
+        if l * l + m * m < 0.25 and (i, j) not in [(q[0], q[1]) for q in srcs]:
+            amp = noise_sigma * (1.0 - 0.15 * len(srcs))
+            srcs.append((i, j, amp))
+            lm_amp.append((l, m, amp))
+    sky = np.empty_like(w.volts)
+    for c in range(w.n_chan):
+        z = _source_block(rng_s, w.ant_xy, w.freq_hz[c:c + 1], w.n_time, 2, lm_amp)
+        sky[:, c:c + 1] = quantize4(z)
+    sky_w = Workload("sky", w.ant_xy, w.freq_hz, 2, w.grid_n, w.support, w.cell_lambda, w.sigma_cells, sky,
+                     sources=srcs)
+    w.name = "differentiation"
+    return w, sky_w
