@@ -129,7 +129,7 @@ def test_autograd_function():
         l = autograd.calib_loss(plan, dv, g, model)
         l.backward()
         opt.step()
-        losses.append(float(l))
+        losses.append(float(l.detach()))
     assert losses[-1] < losses[0]
     plan.close()
 
