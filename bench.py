@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--soak-seconds", type=float, default=1.5)
+    ap.add_argument("--grad-steps", type=int, default=20,
+                    help="epic_grad calls timed on the gain-calibration config (0: skip)")
     return ap.parse_args()
 
 
@@ -356,6 +358,40 @@ def main():
                "h2d_bytes_per_step": int(w.volts.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 4),
                "steps": args.e2e_steps, "api": "epic_image_host (pinned host buffers, synchronous)"}
 
+    # gain calibration (differentiation config): loss + gradient per block
+    grad = None
+    if args.grad_steps > 0:
+        wg, sky = synth.differentiation()
+        gplan = epic.plan_for(wg)
+        dvg = torch.from_numpy(wg.volts).cuda()
+        model_full = torch.empty(gplan.out_shape, dtype=torch.float32, device="cuda")
+        splan = epic.plan_for(sky)  # model: the noise-free 5-source sky imaged with unit gains
+        epic.epic_image(splan, torch.from_numpy(sky.volts).cuda(), sky.n_time, model_full, 0)
+        model = model_full[:, :2].contiguous()
+        gains = torch.from_numpy(np.stack([wg.gains.real, wg.gains.imag], -1).astype(np.float32)).cuda()
+        g_out = torch.empty_like(gains)
+        loss = torch.empty((), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            epic.epic_grad(gplan, dvg, wg.n_time, gains, model, g_out, loss)
+        torch.cuda.synchronize()
+        epic.epic_timing_enable(gplan, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.grad_steps):
+            epic.epic_grad(gplan, dvg, wg.n_time, gains, model, g_out, loss)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / args.grad_steps
+        gkt = epic.epic_timing_read(gplan)
+        grad = {"workload": "gain calibration: station block with seeded gains (|g| 1 +- 0.1, phase +- 0.3 rad), "
+                            "model = 5-source noise-free sky imaged with unit gains",
+                "ms_per_call": gms, "value": wg.units / (gms / 1e3), "unit": UNIT,
+                "loss": float(loss.item()),
+                "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in gkt.items()}}
+        gplan.close()
+        splan.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
@@ -375,7 +411,7 @@ def main():
                                  f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
                 "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": primary["gpu_launches"], "kernel_times_ms": primary["kernel_times_ms"],
-                "paths": others, "clocks": clocks}
+                "paths": others, "grad": grad, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

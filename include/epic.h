@@ -199,6 +199,24 @@ epic_status epic_image_noalloc(epic_plan* plan, const uint8_t* d_volts, int n_ti
 epic_status epic_grad(epic_plan* plan, const uint8_t* d_volts, int n_time, const float* d_gains,
                       const float* d_model, float* d_grad, float* d_loss, void* stream);
 
+/* Post-processing flags of epic_postprocess. */
+#define EPIC_POST_STOKES 1  /* planes -> pseudo-Stokes I, Q, U, V                     */
+#define EPIC_POST_BEAM 2    /* divide by the image of the illumination kernels        */
+
+/* Post-processes accumulated images (layout of epic_image's output):
+ *   EPIC_POST_STOKES: pseudo-Stokes planes of linear feeds (Sec. 4.3: straight
+ *     linear combinations of the coherency products): I = XX + YY,
+ *     Q = XX - YY, U = XY + YX = 2 Re XY, V = -i (XY - YX) = 2 Im XY, with
+ *     YX = conj XY.  Needs a two-polarisation plan.
+ *   EPIC_POST_BEAM: every plane divided by the channel's kernel imprint
+ *     B(l,m) = (1/n_ant) sum_a |W_a(l,m)|^2 (Sec. 3.2, last paragraph: the
+ *     image of the pre-generated gridding kernels, removed after the fact);
+ *     pixels with B < beam_floor are set to 0.  B = 1 at the zero frequency.
+ * Both flags together apply the Stokes step first.  d_in and d_out are device
+ * [n_chan][4][N][N] float and may be the same buffer.  beam_floor > 0. */
+epic_status epic_postprocess(const epic_plan* plan, const float* d_in, float* d_out, int flags,
+                             float beam_floor, void* stream);
+
 /* Waits for the stream and reports any device-side error recorded by the
  * plan's kernels since the previous call (EPIC_ERR_TIMEOUT, EPIC_ERR_CUDA). */
 epic_status epic_sync(epic_plan* plan, void* stream);

@@ -84,6 +84,8 @@ def _load():
             lib.eo_max_threads.restype = ctypes.c_int
             lib.eo_grad_fx.argtypes = [A, _U8, ctypes.c_int, _D, _D, _D]
             lib.eo_grad_fx.restype = ctypes.c_int
+            lib.eo_beam.argtypes = [A, ctypes.c_int, _D]
+            lib.eo_stokes.argtypes = [ctypes.c_int, _D, _D]
             _lib = lib
     return _lib
 
@@ -299,3 +301,18 @@ def loss_epic(arr: OracleArray, volts, model) -> float:
     m = np.asarray(model, np.float64).reshape(arr.n_chan, 2, arr.grid_n, arr.grid_n)
     planes = [0] if arr.n_pol == 1 else [0, 1]
     return float(sum(np.sum((img[:, p] - m[:, p]) ** 2) for p in planes))
+
+
+def beam(arr: OracleArray, c: int) -> np.ndarray:
+    """Image of the illumination kernels of channel c: mean_a |W_a|^2, [N][N]."""
+    out = np.zeros((arr.grid_n, arr.grid_n), np.float64)
+    _load().eo_beam(arr.ref, c, _dptr(out))
+    return out
+
+
+def stokes(img4) -> np.ndarray:
+    """Pseudo-Stokes I, Q, U, V planes from XX, YY, Re XY, Im XY ([4][N][N])."""
+    x = np.ascontiguousarray(img4, np.float64)
+    out = np.zeros_like(x)
+    _load().eo_stokes(x.shape[-1] * x.shape[-2], _dptr(x), _dptr(out))
+    return out

@@ -655,3 +655,34 @@ int eo_grad_fx(const eo_array* d, const uint8_t* volts, int T, const double* mod
   free(v); free(wr); free(wi); free(img);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Post-processing (Sec. 3.2 last paragraph; Sec. 4.3).                      */
+/* eo_beam: image of the illumination kernels of channel c, the mean over    */
+/* antennas of |W_a(l,m)|^2 ([N][N]).                                        */
+/* eo_stokes: pseudo-Stokes planes of linear feeds from [4][N][N] XX, YY,    */
+/* Re XY, Im XY: I = XX + YY, Q = XX - YY, U = XY + YX, V = -i (XY - YX),    */
+/* with YX = conj(XY).                                                       */
+/* ------------------------------------------------------------------------ */
+void eo_beam(const eo_array* d, int c, double* beam) {
+  const int NN = d->grid_n * d->grid_n;
+  double* wp = (double*)malloc(sizeof(double) * NN);
+  memset(beam, 0, sizeof(double) * NN);
+  for (int a = 0; a < d->n_ant; ++a) {
+    eo_kernel_power(d, c, a, wp);
+    for (int k = 0; k < NN; ++k) beam[k] += wp[k];
+  }
+  for (int k = 0; k < NN; ++k) beam[k] /= d->n_ant;
+  free(wp);
+}
+
+void eo_stokes(int NN, const double* in, double* out) {
+  for (int k = 0; k < NN; ++k) {
+    const double xx = in[k], yy = in[NN + k], xyr = in[2 * NN + k], xyi = in[3 * NN + k];
+    /* YX = conj(XY): XY + YX = 2 Re XY; -i (XY - YX) = -i (2 i Im XY) = 2 Im XY */
+    out[k] = xx + yy;
+    out[NN + k] = xx - yy;
+    out[2 * NN + k] = 2.0 * xyr;
+    out[3 * NN + k] = 2.0 * xyi;
+  }
+}

@@ -61,7 +61,7 @@ void free_plan(Plan& p) {
   void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
                   p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
                   p.d_stage_in, p.d_stage_out, p.d_fmat, p.d_dphase, p.d_gcoef, p.d_gcoef64, p.d_gimage,
-                  p.d_resid, p.d_loss_part, p.d_gpart};
+                  p.d_resid, p.d_loss_part, p.d_gpart, p.d_beam};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   epic::free_gather_tables(p.gt);
@@ -234,6 +234,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   EPIC_TRY(alloc(&p.d_dphase, C * A * P, &total));
   EPIC_TRY(alloc(&p.d_kx2, C * A * N, &total));
   EPIC_TRY(alloc(&p.d_ky2, C * A * N, &total));
+  EPIC_TRY(alloc(&p.d_beam, C * N * N, &total));
   EPIC_TRY(alloc(&p.d_csr_ptr, C * (N * N + 1), &total));
   EPIC_TRY(alloc(&p.d_csr_ent, C * A * S * S, &total));
   EPIC_TRY(alloc(&p.d_twiddle, N, &total));
@@ -248,6 +249,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   EPIC_TRY(epic::launch_plan_terms(p, 0));
   EPIC_TRY(epic::launch_twiddles(p, 0));
   EPIC_TRY(epic::launch_build_csr(p, 0));
+  EPIC_TRY(epic::launch_beam(p, 0));
   EPIC_TRY(cudaDeviceSynchronize());
   int status = 0, nnz_last = 0;
   EPIC_TRY(cudaMemcpy(&status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -408,6 +410,15 @@ epic_status epic_grad(epic_plan* h, const uint8_t* d_volts, int n_time, const fl
   if (e == cudaSuccess) e = timed(p, "adjoint", s, [&] { return epic::launch_adjoint(p, d_volts, n_time, ws, s); });
   if (e == cudaSuccess) e = epic::launch_grad_reduce(p, n_time, ws, d_gains, d_grad, s);
   return from_cuda(e);
+}
+
+epic_status epic_postprocess(const epic_plan* h, const float* d_in, float* d_out, int flags, float beam_floor,
+                             void* stream) {
+  if (!h || !d_in || !d_out || (flags & ~(EPIC_POST_STOKES | EPIC_POST_BEAM)) != 0 || !(beam_floor > 0.f))
+    return EPIC_ERR_INVALID_ARG;
+  if ((flags & EPIC_POST_STOKES) && h->p.P != 2) return EPIC_ERR_INVALID_ARG;
+  return from_cuda(epic::launch_postprocess(h->p, d_in, d_out, flags, beam_floor,
+                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
 epic_status epic_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, void* stream) {

@@ -56,6 +56,7 @@ struct Plan {
   double2* d_dphase = nullptr;  // [C][A][P] delay phase exp(-2 pi i nu tau) alone (FP64)
   float* d_kx2 = nullptr;       // [C][A][N] |FT of w_x|^2 per output column
   float* d_ky2 = nullptr;       // [C][A][N] |FT of w_y|^2 per output row
+  float* d_beam = nullptr;      // [C][N][N] kernel imprint (1/A) sum_a |W_a|^2
   int* d_csr_ptr = nullptr;     // [C][N*N+1] gather table: cell -> entries
   int2* d_csr_ent = nullptr;    // [C][A*S*S] (antenna, weight bits), antenna order
   float2* d_twiddle = nullptr;  // [N] exp(+2 pi i m / N)
@@ -101,6 +102,9 @@ struct Plan {
 cudaError_t launch_plan_terms(Plan& p, cudaStream_t s);
 cudaError_t launch_build_csr(Plan& p, cudaStream_t s);
 cudaError_t launch_twiddles(Plan& p, cudaStream_t s);
+cudaError_t launch_beam(Plan& p, cudaStream_t s);
+cudaError_t launch_postprocess(const Plan& p, const float* d_in, float* d_out, int flags, float floor,
+                               cudaStream_t s);
 // Builds p.gt from the per-cell table (two launches, synchronous).
 cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, size_t* bytes);
 void free_gather_tables(GatherTables& g);

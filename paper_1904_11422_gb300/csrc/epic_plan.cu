@@ -172,7 +172,29 @@ __global__ void __launch_bounds__(kCsrThreads) build_csr_kernel(int A, int N, in
   if (tid == blockDim.x - 1) ptr[NN] = tsum[tid];
 }
 
+// Image of the illumination kernels (Sec. 3.2, last paragraph: "the imprint of
+// the image of the gridding illumination kernels"): B_c(l,m) = (1/A) sum_a
+// |W_a(l,m)|^2, each factor the product of the antenna's 1-D power spectra;
+// 1 at the zero frequency since every kernel sums to 1.
+__global__ void beam_kernel(int A, int N, const float* __restrict__ kx2, const float* __restrict__ ky2,
+                            float* __restrict__ beam) {
+  const int c = blockIdx.y;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= N * N) return;
+  const int j = pix / N, i = pix % N;
+  double s = 0.0;
+  for (int a = 0; a < A; ++a)
+    s += (double)kx2[((size_t)c * A + a) * N + i] * (double)ky2[((size_t)c * A + a) * N + j];
+  beam[(size_t)c * N * N + pix] = (float)(s / A);
+}
+
 }  // namespace
+
+cudaError_t launch_beam(Plan& p, cudaStream_t s) {
+  dim3 grid((p.N * p.N + 255) / 256, p.C);
+  beam_kernel<<<grid, 256, 0, s>>>(p.A, p.N, p.d_kx2, p.d_ky2, p.d_beam);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_plan_terms(Plan& p, cudaStream_t s) {
   const long long n = (long long)p.C * p.A;

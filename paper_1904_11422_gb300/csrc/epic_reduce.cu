@@ -86,6 +86,35 @@ __global__ void __launch_bounds__(kReduceThreads)
   }
 }
 
+// Post-processing of accumulated images, one thread per (channel, pixel):
+// pseudo-Stokes planes from the coherencies of linear feeds (Sec. 4.3: linear
+// combinations of the coherency products; YX = conj XY) and division by the
+// kernel imprint (Sec. 3.2, last paragraph).
+__global__ void postprocess_kernel(int C, int NN, int flags, float floor, const float* __restrict__ beam,
+                                   const float* in, float* out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)C * NN) return;
+  const size_t c = idx / NN, pix = idx % NN;
+  float v[4];
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl) v[pl] = in[(c * 4 + pl) * NN + pix];
+  if (flags & EPIC_POST_STOKES) {
+    const float xx = v[0], yy = v[1], xyr = v[2], xyi = v[3];
+    v[0] = xx + yy;          // I
+    v[1] = xx - yy;          // Q
+    v[2] = 2.f * xyr;        // U = XY + YX
+    v[3] = 2.f * xyi;        // V = -i (XY - YX)
+  }
+  if (flags & EPIC_POST_BEAM) {
+    const float b = beam[c * NN + pix];
+    const float scale = b >= floor ? 1.f / b : 0.f;
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl) v[pl] *= scale;
+  }
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl) out[(c * 4 + pl) * NN + pix] = v[pl];
+}
+
 __global__ void zero_kernel(float* __restrict__ out, size_t n) {
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
     out[k] = 0.f;
@@ -145,6 +174,14 @@ cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double
   dim3 grid(p.C, p.N / rows);
   fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, p.spans, p.subtract, 0, rows, p.d_part,
                                         p.d_part_auto, coef64, p.d_kx2, p.d_ky2, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_postprocess(const Plan& p, const float* d_in, float* d_out, int flags, float floor,
+                               cudaStream_t s) {
+  const size_t n = (size_t)p.C * p.N * p.N;
+  postprocess_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.C, p.N * p.N, flags, floor, p.d_beam, d_in,
+                                                                   d_out);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,9 @@ EPIC_XFORM_DFT_FP16X3 = 2
 EPIC_XFORM_DFT_BF16 = 3
 EPIC_XFORM_DFT_FP16 = 4
 
+EPIC_POST_STOKES = 1
+EPIC_POST_BEAM = 2
+
 XFORMS = {"fft_fp32": 0, "dft_bf16x3": 1, "dft_fp16x3": 2, "dft_bf16": 3, "dft_fp16": 4}
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -76,6 +79,7 @@ SIGNATURES = {
     "epic_image_noalloc": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_sync": (_I, [_P, _P]),
     "epic_grad": (_I, [_P, _P, _I, _P, _P, _P, _P, _P]),
+    "epic_postprocess": (_I, [_P, _P, _P, _I, ctypes.c_float, _P]),
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
@@ -262,6 +266,13 @@ def epic_grad(plan: Plan, d_volts, n_time: int, d_gains, d_model, d_grad, d_loss
                                     _dev_tensor(d_model, "float32", "d_model"),
                                     _dev_tensor(d_grad, "float32", "d_grad"),
                                     _dev_tensor(d_loss, "float32", "d_loss"), _stream(stream)), "epic_grad")
+
+
+def epic_postprocess(plan: Plan, d_in, d_out, flags: int, beam_floor: float = 1e-3, stream=None) -> None:
+    """Pseudo-Stokes planes and/or kernel-imprint division (see include/epic.h)."""
+    _check(load_library().epic_postprocess(plan.handle, _dev_tensor(d_in, "float32", "d_in"),
+                                           _dev_tensor(d_out, "float32", "d_out"), int(flags),
+                                           float(beam_floor), _stream(stream)), "epic_postprocess")
 
 
 def epic_sync(plan: Plan, stream=None) -> None:

@@ -212,3 +212,29 @@ def test_plan_create_errors(torch):
     with pytest.raises(epic.EpicError):
         epic.epic_image(plan, dv, 1, out, 2)
     plan.close()
+
+
+def test_postprocess_matches_oracle(torch):
+    w = synth.random_small(1501, n_ant=20, n_pol=2, n_chan=3, grid_n=64, support=5, n_time=6)
+    plan = epic.plan_for(w)
+    dv = torch.from_numpy(w.volts).cuda()
+    img = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    epic.epic_image(plan, dv, w.n_time, img, 0)
+    ref = oracle_image(w)
+    arr = oracle_array(w)
+    floor = 0.05
+    for flags in (epic.EPIC_POST_STOKES, epic.EPIC_POST_BEAM, epic.EPIC_POST_STOKES | epic.EPIC_POST_BEAM):
+        out = torch.empty_like(img)
+        epic.epic_postprocess(plan, img, out, flags, floor)
+        epic.epic_sync(plan)
+        got = out.cpu().numpy()
+        exp = ref.copy()
+        for c in range(w.n_chan):
+            if flags & epic.EPIC_POST_STOKES:
+                exp[c] = oracle.stokes(exp[c])
+            if flags & epic.EPIC_POST_BEAM:
+                b = oracle.beam(arr, c)
+                exp[c] = np.where(b >= floor, exp[c] / np.maximum(b, floor), 0.0)
+        scale = np.abs(exp).max()
+        assert np.abs(got - exp).max() <= 1e-5 * scale
+    plan.close()

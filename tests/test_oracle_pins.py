@@ -399,3 +399,38 @@ def test_gradient_fx_closed_form_matches_finite_differences(oracle_lib, seed, kw
             lm = oracle.loss_epic(_arr(w, gains=gm), w.volts, model)
             fd += unit * (lp - lm) / (2 * h)
         assert abs(fd - grad[c, a, p]) <= 1e-6 * scale, (c, a, p, fd, grad[c, a, p])
+
+
+# --------------------------------------------------------------------------
+# Post-processing: kernel imprint and pseudo-Stokes
+# --------------------------------------------------------------------------
+def test_beam_is_one_at_zero_frequency_and_bounded(oracle_lib):
+    w = synth.random_small(1401, n_ant=6, n_pol=2, n_chan=2, grid_n=16, support=5)
+    arr = _arr(w)
+    for c in range(2):
+        b = oracle.beam(arr, c)
+        N = w.grid_n
+        assert b[N // 2, N // 2] == pytest.approx(1.0, abs=1e-14)  # every kernel sums to 1
+        assert b.max() <= 1.0 + 1e-14 and b.min() >= 0.0
+        # S = 1: a single unit weight, flat imprint
+    arr1 = oracle.OracleArray(w.ant_xy, w.freq_hz, 2, w.grid_n, 1, 0.5, 0.25)
+    assert np.allclose(oracle.beam(arr1, 0), 1.0, atol=1e-14)
+
+
+def test_stokes_of_unpolarised_and_linear_sources(oracle_lib):
+    # closed forms: an unpolarised source (Y_X, Y_Y independent, equal power) has
+    # Q = U = V = 0 in expectation; a source with Y_Y = Y_X has I = 2 XX, Q = 0, U = I
+    rng = np.random.default_rng(5)
+    N = 4
+    yx = rng.standard_normal((200, N, N)) + 1j * rng.standard_normal((200, N, N))
+    img = np.stack([np.sum(np.abs(yx) ** 2, 0), np.sum(np.abs(yx) ** 2, 0),
+                    np.sum((yx * np.conj(yx)).real, 0), np.sum((yx * np.conj(yx)).imag, 0)])
+    st = oracle.stokes(img)
+    assert np.allclose(st[0], 2 * img[0]) and np.allclose(st[1], 0) and np.allclose(st[2], st[0])
+    assert np.allclose(st[3], 0)
+    # circular: Y_Y = -i Y_X gives XY = Y_X conj(Y_Y) = i |Y_X|^2, so V = 2 |Y_X|^2 = I
+    yy = -1j * yx
+    img = np.stack([np.sum(np.abs(yx) ** 2, 0), np.sum(np.abs(yy) ** 2, 0),
+                    np.sum((yx * np.conj(yy)).real, 0), np.sum((yx * np.conj(yy)).imag, 0)])
+    st = oracle.stokes(img)
+    assert np.allclose(st[3], st[0]) and np.allclose(st[1], 0) and np.allclose(st[2], 0)
