@@ -217,6 +217,32 @@ epic_status epic_grad(epic_plan* plan, const uint8_t* d_volts, int n_time, const
 epic_status epic_postprocess(const epic_plan* plan, const float* d_in, float* d_out, int flags,
                              float beam_floor, void* stream);
 
+/* A batch: several imaging problems (arrays of different antenna counts, grid
+ * sizes and channel counts, each with its own plan) run by one graph launch. */
+typedef struct epic_batch epic_batch;
+
+/* Captures the imaging launches of n_plans plans (distinct plans, 1..64) into
+ * one CUDA graph, each plan on its own branch so the arrays run concurrently.
+ * d_volts[i], n_time[i], d_out[i] are plan i's arguments as in epic_image
+ * (accumulate = 0); the pointers are baked into the graph and must stay valid
+ * while the batch exists (their contents may change between launches).
+ * tune = 1 runs the autotuner first: it times candidate graphs (each plan's
+ * CTA count, i.e. its time-tile length: all SMs, shares proportional to the
+ * plans' work, halved and quartered caps) and keeps the fastest; this launches
+ * the imaging kernels several times on `stream` and overwrites d_out.
+ * chosen_ctas (optional, [n_plans]) receives the CTA caps in the graph.
+ * Synchronous.  Results equal epic_image's exactly when tune = 0, and up to the
+ * summation order of the partial images (FP32 rounding) when tune = 1. */
+epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_t* const* d_volts,
+                              const int* n_time, float* const* d_out, int tune, int* chosen_ctas,
+                              void* stream, epic_batch** out);
+
+/* One launch of the batch's graph on stream (asynchronous). */
+epic_status epic_batch_launch(epic_batch* batch, void* stream);
+
+/* Frees the batch (synchronises the device); the plans are not destroyed. */
+epic_status epic_batch_destroy(epic_batch* batch);
+
 /* Waits for the stream and reports any device-side error recorded by the
  * plan's kernels since the previous call (EPIC_ERR_TIMEOUT, EPIC_ERR_CUDA). */
 epic_status epic_sync(epic_plan* plan, void* stream);

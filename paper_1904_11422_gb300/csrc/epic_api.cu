@@ -67,17 +67,6 @@ void free_plan(Plan& p) {
   epic::free_gather_tables(p.gt);
 }
 
-// Work units u = c*T + t (channel-major) split into equal contiguous ranges,
-// one per CTA, with no CTA left empty.
-epic::WorkSplit split_work(const Plan& p, int T) {
-  epic::WorkSplit ws;
-  ws.T = T;
-  ws.units = (long long)p.C * T;
-  long long ctas = p.ctas < ws.units ? p.ctas : ws.units;
-  ws.W = (ws.units + ctas - 1) / ctas;
-  ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);
-  return ws;
-}
 
 cudaEvent_t take_event(Plan& p) {
   if (!p.event_pool.empty()) {
@@ -137,6 +126,44 @@ int spans_needed(const epic::WorkSplit& ws) {
   }
   return worst;
 }
+
+// Work units u = c*T + t (channel-major) split into equal contiguous ranges,
+// one per CTA (at most `cap` CTAs), with no CTA left empty.
+epic::WorkSplit split_work_cap(const Plan& p, int T, int cap) {
+  epic::WorkSplit ws;
+  ws.T = T;
+  ws.units = (long long)p.C * T;
+  long long ctas = cap < ws.units ? cap : ws.units;
+  ws.W = (ws.units + ctas - 1) / ctas;
+  ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);
+  ws.spans = spans_needed(ws);
+  return ws;
+}
+
+epic::WorkSplit split_work(const Plan& p, int T) { return split_work_cap(p, T, p.ctas_use > 0 ? p.ctas_use : p.ctas); }
+
+bool split_fits(const Plan& p, const epic::WorkSplit& ws) {
+  return (long long)ws.ctas * ws.spans <= (long long)p.ctas * p.spans;
+}
+
+}  // namespace
+
+namespace epic {
+// The launches of one imaging call (image kernel, then the block-end reduction),
+// shared by epic_image and the batch graphs.  No timing, no allocation.
+cudaError_t image_launches(Plan& p, const uint8_t* d_volts, int n_time, float* d_out, int accumulate, cudaStream_t s) {
+  const size_t out_n = (size_t)p.C * 4 * p.N * p.N;
+  if (n_time == 0) return accumulate ? cudaSuccess : launch_zero(d_out, out_n, s);
+  const WorkSplit ws = split_work(p, n_time);
+  if (!split_fits(p, ws)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = (p.xform == EPIC_XFORM_FFT_FP32) ? launch_fft_image(p, d_volts, n_time, ws, s)
+                                                   : launch_dft_image(p, d_volts, n_time, ws, p.d_part, p.d_part_auto, s);
+  if (e != cudaSuccess) return e;
+  return launch_reduce(p, n_time, ws, d_out, accumulate, s);
+}
+}  // namespace epic
+
+namespace {
 
 }  // namespace
 
@@ -339,7 +366,7 @@ epic_status epic_image(epic_plan* h, const uint8_t* d_volts, int n_time, float* 
   const size_t out_n = (size_t)p.C * 4 * p.N * p.N;
   if (n_time == 0) return accumulate ? EPIC_OK : from_cuda(epic::launch_zero(d_out, out_n, s));
   const epic::WorkSplit ws = split_work(p, n_time);
-  if (spans_needed(ws) > p.spans) return EPIC_ERR_CUDA;  // cannot happen: spans sized for any n_time
+  if (!split_fits(p, ws)) return EPIC_ERR_UNSUPPORTED;  // a CTA cap below the plan's needs more slots
   cudaError_t e = (p.xform == EPIC_XFORM_FFT_FP32)
                       ? timed(p, "fft_image", s, [&] { return epic::launch_fft_image(p, d_volts, n_time, ws, s); })
                       : timed(p, "dft_image", s, [&] {
@@ -401,6 +428,7 @@ epic_status epic_grad(epic_plan* h, const uint8_t* d_volts, int n_time, const fl
   if (!p.grad_ok) return EPIC_ERR_UNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const epic::WorkSplit ws = split_work(p, n_time);
+  if (!split_fits(p, ws)) return EPIC_ERR_UNSUPPORTED;
   cudaError_t e = epic::launch_grad_coef(p, d_gains, s);
   if (e == cudaSuccess)
     e = timed(p, "fft_image", s, [&] { return epic::launch_fft_image_coef(p, d_volts, n_time, ws, p.d_gcoef, s); });

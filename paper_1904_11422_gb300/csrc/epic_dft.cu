@@ -588,7 +588,7 @@ template <int XF>
 cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                        int* part_auto, cudaStream_t s) {
   dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(
-      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
       p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, reinterpret_cast<const uint32_t*>(p.d_fmat),
       part, part_auto, p.d_status);
   return cudaGetLastError();

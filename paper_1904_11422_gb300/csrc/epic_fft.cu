@@ -423,7 +423,7 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
-      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
+      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
       p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
@@ -439,7 +439,7 @@ cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, co
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
-      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
+      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
       p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, part, part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
@@ -760,7 +760,7 @@ cudaError_t launch_fft_image_coef(Plan& p, const uint8_t* d_volts, int T, const 
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
-      d_volts, T, p.C, p.A, ws.W, ws.units, p.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,            \
+      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,            \
       p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
   if (p.N == 64) {
     if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
@@ -787,7 +787,7 @@ cudaError_t launch_adjoint(Plan& p, const uint8_t* d_volts, int T, const WorkSpl
   auto fn = p.P == 2 ? adjoint_kernel<2> : adjoint_kernel<1>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<ws.ctas, 512, smem, s>>>(d_volts, T, p.C, p.A, p.S, ws.W, ws.units, p.spans, p.d_gcoef, p.d_dphase,
+  fn<<<ws.ctas, 512, smem, s>>>(d_volts, T, p.C, p.A, p.S, ws.W, ws.units, ws.spans, p.d_gcoef, p.d_dphase,
                                  p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off, p.gt.d_ent_a, p.gt.d_ent_w,
                                  p.gt.max_chan_entries, ent, p.d_twiddle, p.d_resid, p.d_box, p.d_wx, p.d_wy,
                                  p.d_gpart);

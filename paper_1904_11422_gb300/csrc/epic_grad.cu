@@ -125,7 +125,7 @@ cudaError_t launch_residual(Plan& p, const float* d_model, float* d_loss, cudaSt
 
 cudaError_t launch_grad_reduce(Plan& p, int T, const WorkSplit& ws, const float* d_gains, float* d_grad,
                                cudaStream_t s) {
-  grad_reduce_kernel<<<p.C, 256, 0, s>>>(T, p.A, p.P, p.N, ws.W, ws.ctas, p.spans, p.subtract, p.d_gpart,
+  grad_reduce_kernel<<<p.C, 256, 0, s>>>(T, p.A, p.P, p.N, ws.W, ws.ctas, ws.spans, p.subtract, p.d_gpart,
                                          p.d_part_auto, p.d_resid, p.d_kx2, p.d_ky2, d_gains, d_grad);
   return cudaGetLastError();
 }

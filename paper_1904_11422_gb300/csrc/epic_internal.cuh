@@ -22,6 +22,7 @@ struct WorkSplit {
   long long units; // C * T
   long long W;     // units per CTA
   int T;
+  int spans;       // partial-image slots per CTA used by this call (ctas * spans fits the workspace)
 };
 
 // Gather tables of a gridder (see epic_gather.cu).
@@ -66,6 +67,7 @@ struct Plan {
 
   // imaging launch shape and its workspace (partial images per CTA span)
   int ctas = 0, threads = 0, spans = 0, ent_in_smem = 0;
+  int ctas_use = 0;  // CTAs an imaging launch may use (0: ctas); set by the batch autotuner
   size_t smem = 0;
   float* d_part = nullptr;      // [ctas][spans][4][N][N]
   int* d_part_auto = nullptr;   // [ctas][spans][A][4] exact integer self powers
@@ -139,6 +141,8 @@ size_t adjoint_smem_need(const Plan& p);
 cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int accumulate,
                           cudaStream_t s);
 cudaError_t launch_zero(float* d_out, size_t n, cudaStream_t s);
+cudaError_t image_launches(Plan& p, const uint8_t* d_volts, int n_time, float* d_out, int accumulate,
+                           cudaStream_t s);
 
 // The same two launches with the partial-image workspace passed explicitly
 // (used by the entry point that allocates nothing and takes its workspace from

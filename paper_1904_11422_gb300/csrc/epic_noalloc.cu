@@ -76,6 +76,7 @@ extern "C" epic_status epic_image_noalloc(epic_plan* h, const uint8_t* d_volts, 
   const long long ctas = p.ctas < ws.units ? p.ctas : ws.units;
   ws.W = (ws.units + ctas - 1) / ctas;
   ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);
+  ws.spans = p.spans;
 
   // Partial images [ctas][spans][4][N][N] float, then self powers
   // [ctas][spans][A][4] int.  Every slot the reduction reads is written by the

@@ -140,7 +140,7 @@ cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, p.N / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, p.spans, p.subtract, accumulate, rows,
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
                                         p.d_part, p.d_part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }
@@ -156,7 +156,7 @@ cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const fl
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, p.N / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, p.spans, p.subtract, accumulate, rows,
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
                                         part, part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }
@@ -172,7 +172,7 @@ cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, p.N / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, p.spans, p.subtract, 0, rows, p.d_part,
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, ws.spans, p.subtract, 0, rows, p.d_part,
                                         p.d_part_auto, coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }

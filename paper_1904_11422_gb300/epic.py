@@ -80,6 +80,10 @@ SIGNATURES = {
     "epic_sync": (_I, [_P, _P]),
     "epic_grad": (_I, [_P, _P, _I, _P, _P, _P, _P, _P]),
     "epic_postprocess": (_I, [_P, _P, _P, _I, ctypes.c_float, _P]),
+    "epic_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P),
+                               _I, ctypes.POINTER(_I), _P, ctypes.POINTER(_P)]),
+    "epic_batch_launch": (_I, [_P, _P]),
+    "epic_batch_destroy": (_I, [_P]),
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
@@ -273,6 +277,49 @@ def epic_postprocess(plan: Plan, d_in, d_out, flags: int, beam_floor: float = 1e
     _check(load_library().epic_postprocess(plan.handle, _dev_tensor(d_in, "float32", "d_in"),
                                            _dev_tensor(d_out, "float32", "d_out"), int(flags),
                                            float(beam_floor), _stream(stream)), "epic_postprocess")
+
+
+class Batch:
+    """Owns an ``epic_batch*`` and keeps its plans and buffers alive."""
+
+    def __init__(self, handle, plans, buffers, ctas):
+        self.handle = handle
+        self.plans = plans
+        self._buffers = buffers
+        self.ctas = ctas
+
+    def close(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            epic_batch_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def epic_batch_create(plans, d_volts, n_time, d_out, tune: bool = False, stream=None) -> Batch:
+    n = len(plans)
+    hp = (_P * n)(*[p.handle for p in plans])
+    hv = (_P * n)(*[_dev_tensor(v, "uint8", "d_volts") for v in d_volts])
+    ht = (_I * n)(*[int(t) for t in n_time])
+    ho = (_P * n)(*[_dev_tensor(o, "float32", "d_out") for o in d_out])
+    chosen = (_I * n)()
+    h = _P()
+    _check(load_library().epic_batch_create(hp, n, hv, ht, ho, int(bool(tune)), chosen, _stream(stream),
+                                            ctypes.byref(h)), "epic_batch_create")
+    return Batch(h.value, list(plans), (list(d_volts), list(d_out)), list(chosen))
+
+
+def epic_batch_launch(batch: Batch, stream=None) -> None:
+    _check(load_library().epic_batch_launch(batch.handle, _stream(stream)), "epic_batch_launch")
+
+
+def epic_batch_destroy(batch) -> None:
+    h = batch.handle if isinstance(batch, Batch) else batch
+    _check(load_library().epic_batch_destroy(h), "epic_batch_destroy")
 
 
 def epic_sync(plan: Plan, stream=None) -> None:

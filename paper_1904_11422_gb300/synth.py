@@ -238,3 +238,34 @@ def differentiation(config_index: int = 4, n_chan: int = 64, n_time: int = 1250,
                      sources=srcs)
     w.name = "differentiation"
     return w, sky_w
+
+
+def batching_array(which: str, config_index: int = 3, n_time: int = 1250) -> Workload:
+    """The arrays of the batching recipe, all dual-pol over 60-76 MHz with
+    station-style noise + 3 point sources:
+      'A': 64 antennas in a 50 m disk (min spacing 3 m), 32x32 grid, 16 channels, 3x3 kernel;
+      'B': the station array (256 antennas, 110 m, 64x64, 64 channels, 5x5);
+      'C': 1024 antennas in a 220 m disk (min spacing 3 m), 128x128 grid, 32 channels, 5x5."""
+    spec = {"A": (64, 50.0, 3.0, 32, 16, 3), "B": (256, 110.0, 5.0, 64, 64, 5), "C": (1024, 220.0, 3.0, 128, 32, 5)}
+    A, diam, dmin, N, C, S = spec[which]
+    base = 100 * config_index + {"A": 0, "B": 10, "C": 20}[which]
+    ant = disk_positions(A, diam, dmin, 1 + base)
+    freq = np.linspace(60e6, 76e6, C)
+    rng_v = np.random.default_rng(2 + base)
+    rng_s = np.random.default_rng(3 + base)
+    srcs, lm_amp = [], []
+    sigma = 2.5
+    for amp in (1.0, 0.7, 0.5):
+        while True:
+            i, j = (int(x) for x in rng_s.integers(0, N, size=2))
+            l, m = pixel_direction(N, 0.5, i, j)
+            if l * l + m * m < 0.25 and (i, j) not in [(q[0], q[1]) for q in srcs]:
+                break
+        srcs.append((i, j, amp * sigma))
+        lm_amp.append((l, m, amp * sigma))
+    volts = np.empty((n_time, C, A, 2), np.uint8)
+    for c in range(C):
+        z = sigma * (rng_v.standard_normal((n_time, 1, A, 2)) + 1j * rng_v.standard_normal((n_time, 1, A, 2)))
+        z += _source_block(rng_s, ant, freq[c:c + 1], n_time, 2, lm_amp)
+        volts[:, c:c + 1] = quantize4(z)
+    return Workload(f"batch{which}", ant, freq, 2, N, S, 0.5, (S - 1) / 4.0, volts, sources=srcs)

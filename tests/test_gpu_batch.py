@@ -1,0 +1,88 @@
+"""Batched imaging: several arrays of different antenna counts, grid sizes and
+channel counts in one graph launch, with and without the autotuner."""
+import numpy as np
+import pytest
+
+from paper_1904_11422_gb300 import build_lib, epic, synth
+
+from _helpers import assert_close, oracle_image, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build_lib.build()
+    return epic.load_library()
+
+
+@pytest.fixture(scope="module")
+def arrays():
+    return [synth.batching_array("A", n_time=300), synth.batching_array("B", n_time=300),
+            synth.random_small(1601, n_ant=40, n_pol=2, n_chan=7, grid_n=64, support=3, n_time=55)]
+
+
+def _setup(ws, xforms):
+    import torch
+    plans = [epic.plan_for(w, epic.XFORMS[x]) for w, x in zip(ws, xforms)]
+    vols = [torch.from_numpy(w.volts).cuda() for w in ws]
+    outs = [torch.empty(p.out_shape, dtype=torch.float32, device="cuda") for p in plans]
+    return plans, vols, outs
+
+
+def _single(plans, vols, ws):
+    import torch
+    res = []
+    for p, v, w in zip(plans, vols, ws):
+        o = torch.empty(p.out_shape, dtype=torch.float32, device="cuda")
+        epic.epic_image(p, v, w.n_time, o, 0)
+        res.append(o)
+    torch.cuda.synchronize()
+    return [r.cpu().numpy() for r in res]
+
+
+def test_batch_equals_single_calls_bit_for_bit(arrays):
+    import torch
+    xforms = ["fft_fp32", "fft_fp32", "dft_bf16x3"]
+    plans, vols, outs = _setup(arrays, xforms)
+    ref = _single(plans, vols, arrays)
+    b = epic.epic_batch_create(plans, vols, [w.n_time for w in arrays], outs, tune=False)
+    for _ in range(2):
+        for o in outs:
+            o.fill_(float("nan"))
+        epic.epic_batch_launch(b)
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert np.array_equal(o.cpu().numpy(), r)
+    b.close()
+    for p in plans:
+        p.close()
+
+
+def test_autotuned_batch_matches_oracle(arrays):
+    import torch
+    xforms = ["fft_fp32", "fft_fp32", "fft_fp32"]
+    plans, vols, outs = _setup(arrays, xforms)
+    ref = _single(plans, vols, arrays)
+    b = epic.epic_batch_create(plans, vols, [w.n_time for w in arrays], outs, tune=True)
+    assert all(1 <= c <= p.info["ctas"] for c, p in zip(b.ctas, plans))
+    epic.epic_batch_launch(b)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert rel_errors(o.cpu().numpy(), r, 2).max() <= 1e-6
+    # array A against the oracle on two channels
+    got = outs[0].cpu().numpy()
+    chans = [0, 15]
+    assert_close(got[chans], oracle_image(arrays[0], channels=chans, use_fft=True), 2)
+    b.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_rejects_bad_arguments(arrays):
+    import torch
+    plans, vols, outs = _setup(arrays[:1], ["fft_fp32"])
+    with pytest.raises(epic.EpicError):
+        epic.epic_batch_create(plans + plans, vols + vols, [300, 300], outs + outs)  # same plan twice
+    for p in plans:
+        p.close()
