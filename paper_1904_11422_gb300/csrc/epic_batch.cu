@@ -8,6 +8,8 @@
 // count (how many SMs its persistent imaging kernel spreads over, i.e. its
 // time-tile length) by timing candidate graphs.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <new>
 #include <vector>
 
@@ -21,6 +23,7 @@ struct epic_batch {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;  // capture stream (the legacy default stream cannot be captured)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> ctas;  // CTA cap of each plan in the captured graph
@@ -30,6 +33,7 @@ namespace {
 
 epic_status status_of(cudaError_t e) {
   if (e == cudaSuccess) return EPIC_OK;
+  if (std::getenv("EPIC_DEBUG")) std::fprintf(stderr, "epic_batch: %s\n", cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return EPIC_ERR_OOM;
   return EPIC_ERR_CUDA;
 }
@@ -41,8 +45,10 @@ void drop_graph(epic_batch* b) {
   b->graph = nullptr;
 }
 
-// Captures every plan's imaging launches with the given CTA caps.
-cudaError_t capture(epic_batch* b, const std::vector<int>& caps, cudaStream_t s0) {
+// Captures every plan's imaging launches with the given CTA caps (on the batch's
+// own capture stream).
+cudaError_t capture(epic_batch* b, const std::vector<int>& caps) {
+  cudaStream_t s0 = b->cap;
   drop_graph(b);
   std::vector<int> saved(b->plans.size());
   for (size_t i = 0; i < b->plans.size(); ++i) {
@@ -137,7 +143,8 @@ epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_
   }
   std::vector<int> caps(n_plans);
   for (int i = 0; i < n_plans; ++i) caps[i] = plans[i]->p.ctas;
-  if (e == cudaSuccess) e = capture(b, caps, s0);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = capture(b, caps);
   if (e == cudaSuccess && tune) {
     // Autotuner: start from every plan on all its CTAs; try CTA shares
     // proportional to each plan's work, then halve / quarter each plan's cap in
@@ -173,7 +180,7 @@ epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_
       bool ok = true;
       for (int i = 0; i < n_plans; ++i) ok = ok && cap_fits(plans[i]->p, n_time[i], t[i]);
       if (!ok) continue;
-      e = capture(b, t, s0);
+      e = capture(b, t);
       float ms = 0.f;
       if (e == cudaSuccess) e = time_graph(b, s0, 3, &ms);
       if (e == cudaSuccess && ms < best) {
@@ -181,7 +188,7 @@ epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_
         best_caps = t;
       }
     }
-    if (e == cudaSuccess) e = capture(b, best_caps, s0);
+    if (e == cudaSuccess) e = capture(b, best_caps);
   }
   if (e != cudaSuccess) {
     epic_batch_destroy(b);
@@ -207,6 +214,7 @@ epic_status epic_batch_destroy(epic_batch* b) {
   for (cudaEvent_t ev : b->joins)
     if (ev) cudaEventDestroy(ev);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return EPIC_OK;
 }

@@ -595,8 +595,8 @@ cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkS
 }
 
 template <int XF>
-cudaError_t dft_attr(size_t smem) {
-  return cudaFuncSetAttribute(dft_image_kernel<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t dft_attr() {
+  return allow_max_smem(dft_image_kernel<XF>);
 }
 
 }  // namespace
@@ -619,10 +619,10 @@ cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
   p.ent_in_smem = 1;
   cudaError_t e;
   switch (p.xform) {
-    case EPIC_XFORM_DFT_BF16X3: e = dft_attr<EPIC_XFORM_DFT_BF16X3>(p.smem); break;
-    case EPIC_XFORM_DFT_FP16X3: e = dft_attr<EPIC_XFORM_DFT_FP16X3>(p.smem); break;
-    case EPIC_XFORM_DFT_BF16: e = dft_attr<EPIC_XFORM_DFT_BF16>(p.smem); break;
-    default: e = dft_attr<EPIC_XFORM_DFT_FP16>(p.smem); break;
+    case EPIC_XFORM_DFT_BF16X3: e = dft_attr<EPIC_XFORM_DFT_BF16X3>(); break;
+    case EPIC_XFORM_DFT_FP16X3: e = dft_attr<EPIC_XFORM_DFT_FP16X3>(); break;
+    case EPIC_XFORM_DFT_BF16: e = dft_attr<EPIC_XFORM_DFT_BF16>(); break;
+    default: e = dft_attr<EPIC_XFORM_DFT_FP16>(); break;
   }
   if (e != cudaSuccess) return e;
   *ctas_per_sm = 1;  // the kernel holds all 512 TMEM columns

@@ -349,13 +349,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 }
 
 template <int N, int P>
-cudaError_t set_attrs(size_t smem) {
-  return cudaFuncSetAttribute(fft_image_kernel<N, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-template <int N, int P>
 cudaError_t occupancy(int threads, size_t smem, int* per_sm) {
-  cudaError_t e = set_attrs<N, P>(smem);
+  cudaError_t e = allow_max_smem(fft_image_kernel<N, P>);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fft_image_kernel<N, P>, threads, smem);
 }
@@ -455,8 +450,7 @@ cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int
   const int nnz = p.A * p.S * p.S;
   const size_t smem = sizeof(float2) * p.A;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(p.P == 2 ? debug_grid_kernel<2> : debug_grid_kernel<1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(p.P == 2 ? debug_grid_kernel<2> : debug_grid_kernel<1>);
     if (e != cudaSuccess) return e;
   }
   if (p.P == 2)
@@ -785,7 +779,7 @@ cudaError_t launch_adjoint(Plan& p, const uint8_t* d_volts, int T, const WorkSpl
   const int ent = adj_smem(p, 1) <= (size_t)optin ? 1 : 0;
   const size_t smem = adj_smem(p, ent);
   auto fn = p.P == 2 ? adjoint_kernel<2> : adjoint_kernel<1>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   fn<<<ws.ctas, 512, smem, s>>>(d_volts, T, p.C, p.A, p.S, ws.W, ws.units, ws.spans, p.d_gcoef, p.d_dphase,
                                  p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off, p.gt.d_ent_a, p.gt.d_ent_w,

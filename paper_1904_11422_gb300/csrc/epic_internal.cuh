@@ -12,6 +12,19 @@
 
 namespace epic {
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum.
+// The attribute belongs to the function, not to a plan, so it is never set to
+// one plan's need: a later, smaller plan would then lower it under the launches
+// (and captured graphs) of a larger one.  Each launch still asks for its own size.
+template <class Fn>
+cudaError_t allow_max_smem(Fn fn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return e;
+}
+
 // Device-side error word values (written by kernels, read by epic_sync).
 enum : int { kDevOk = 0, kDevTimeout = 1, kDevBadIndex = 2, kDevOffGrid = 3 };
 

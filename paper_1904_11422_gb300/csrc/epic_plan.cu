@@ -215,7 +215,7 @@ cudaError_t launch_twiddles(Plan& p, cudaStream_t s) {
 cudaError_t launch_build_csr(Plan& p, cudaStream_t s) {
   const size_t smem = sizeof(int) * (2 * (size_t)p.A + kCsrThreads);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(build_csr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(build_csr_kernel);
     if (e != cudaSuccess) return e;
   }
   build_csr_kernel<<<p.C, kCsrThreads, smem, s>>>(p.A, p.N, p.S, p.d_box, p.d_wx, p.d_wy, p.d_csr_ptr, p.d_csr_ent);

@@ -136,7 +136,7 @@ cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, p.N / rows);
@@ -152,7 +152,7 @@ cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const fl
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, p.N / rows);
@@ -168,7 +168,7 @@ cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, p.N / rows);

@@ -238,3 +238,23 @@ def test_postprocess_matches_oracle(torch):
         scale = np.abs(exp).max()
         assert np.abs(got - exp).max() <= 1e-5 * scale
     plan.close()
+
+
+def test_plans_coexist_after_a_smaller_plan(torch, station):
+    """A kernel's shared-memory limit is a property of the function, not of a
+    plan: creating a plan that needs less shared memory must leave an existing,
+    larger plan of the same kernel working."""
+    big = epic.plan_for(station)
+    dv = torch.from_numpy(station.volts[:40]).cuda()
+    a = torch.empty(big.out_shape, dtype=torch.float32, device="cuda")
+    epic.epic_image(big, dv, 40, a, 0)
+    epic.epic_sync(big)
+    w = synth.random_small(1701, n_ant=12, n_pol=2, n_chan=2, grid_n=64, support=3, n_time=4)
+    small = epic.plan_for(w)
+    b = torch.empty_like(a)
+    epic.epic_image(big, dv, 40, b, 0)
+    epic.epic_sync(big)
+    assert torch.equal(a, b)
+    assert_close(gpu_image(w, plan=small), oracle_image(w), 2)
+    small.close()
+    big.close()
