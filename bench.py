@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--soak-seconds", type=float, default=1.5)
+    ap.add_argument("--batch-steps", type=int, default=20,
+                    help="graph launches timed for the batching workload (0 to skip)")
     ap.add_argument("--grad-steps", type=int, default=20,
                     help="epic_grad calls timed on the gain-calibration config (0: skip)")
     return ap.parse_args()
@@ -231,6 +233,54 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def time_batch(args, epic, synth, torch, stream, world, shard):
+    """Arrays A, B and C of the batching recipe (T = 1250 each), every plan that
+    the library supports in one autotuned graph; also the same plans imaged by
+    separate epic_image calls one after another, for comparison."""
+    ws, plans, skipped = [], [], {}
+    for k in ("A", "B", "C"):
+        w = synth.batching_array(k)
+        try:
+            plans.append(epic.plan_for(w))
+            ws.append(w)
+        except epic.EpicError as e:
+            skipped[k] = epic.epic_status_string(e.status)
+    vols = [torch.from_numpy(w.volts).cuda() for w in ws]
+    outs = [torch.empty(p.out_shape, dtype=torch.float32, device="cuda") for p in plans]
+    b = epic.epic_batch_create(plans, vols, [w.n_time for w in ws], outs, tune=True, stream=stream)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return shard.max_over_ranks(e0.elapsed_time(e1) / n, device="cuda")
+
+    ms = timed(lambda: epic.epic_batch_launch(b, stream), args.batch_steps)
+
+    def separate():
+        for p, v, w, o in zip(plans, vols, ws, outs):
+            epic.epic_image(p, v, w.n_time, o, 0, stream)
+
+    ms_sep = timed(separate, args.batch_steps)
+    units = sum(w.units for w in ws)
+    res = {"workload": "batching arrays " + "+".join(w.name[-1] for w in ws) + ", T = 1250 each, one graph launch",
+           "ms_per_launch": ms, "value": units * world / (ms / 1e3), "unit": UNIT,
+           "units_per_launch": units, "ctas_chosen": dict(zip([w.name for w in ws], b.ctas)),
+           "ms_separate_calls": ms_sep, "graph_launches_per_step": 1,
+           "kernel_launches_per_step": 2 * len(plans), "not_in_batch": skipped}
+    b.close()
+    for p in plans:
+        p.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -392,6 +442,11 @@ def main():
         gplan.close()
         splan.close()
 
+    # batching: the arrays of the batching recipe imaged by one graph launch
+    batch = None
+    if args.batch_steps > 0:
+        batch = time_batch(args, epic, synth, torch, stream, world, shard)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
@@ -411,7 +466,7 @@ def main():
                                  f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
                 "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": primary["gpu_launches"], "kernel_times_ms": primary["kernel_times_ms"],
-                "paths": others, "grad": grad, "clocks": clocks}
+                "paths": others, "grad": grad, "batch": batch, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -27,7 +27,10 @@ double cell_coord(double pos_m, double freq_hz, double cell_lambda, int N) {
 constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA on sm_100/sm_103 (227 KB)
 
 bool grid_supported(int xform, int N, int P, int A, int S) {
-  if (xform == EPIC_XFORM_FFT_FP32) return (N == 32 || N == 64) && A <= kMaxAntFft;
+  if (xform == EPIC_XFORM_FFT_FP32) {
+    if (N == 128) return A <= epic::fft128_max_ant() && epic::fft128_smem_need(A, P) <= kSmemOptin;
+    return (N == 32 || N == 64) && A <= kMaxAntFft;
+  }
   // tensor path: 64 x 64 grids of two polarisations, with the gather entries in
   // shared memory (bounded here by the unpadded count A S^2; the exact padded
   // count is checked when the plan is created)
@@ -293,7 +296,13 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
 
   int per_sm = 0;
   size_t gt_bytes = 0;
-  if (p.xform == EPIC_XFORM_FFT_FP32) {
+  int clusters = 0;  // N = 128: the imaging launch counts clusters of two CTAs
+  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128) {
+    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft128, 1024, 0, &gt_bytes));
+    total += gt_bytes;
+    EPIC_TRY(epic::fft128_config(p, &clusters));
+    if (clusters < 1) return fail(cudaErrorInvalidConfiguration);
+  } else if (p.xform == EPIC_XFORM_FFT_FP32) {
     EPIC_TRY(epic::build_gather_tables(p, p.N == 64 ? epic::kLayoutFft64 : epic::kLayoutFft32,
                                        p.N == 64 ? 512 : 128, 0, &gt_bytes));
     total += gt_bytes;
@@ -311,8 +320,8 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
     EPIC_TRY(cudaDeviceSynchronize());
     EPIC_TRY(epic::dft_image_config(p, &per_sm));
   }
-  if (per_sm < 1) return fail(cudaErrorInvalidConfiguration);
-  p.ctas = p.sm_count * per_sm;
+  if (clusters == 0 && per_sm < 1) return fail(cudaErrorInvalidConfiguration);
+  p.ctas = clusters > 0 ? clusters : p.sm_count * per_sm;
   p.spans = (p.C + p.ctas - 1) / p.ctas + 2;
   size_t before = total;
   EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * N * N, &total));

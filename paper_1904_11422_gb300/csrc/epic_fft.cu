@@ -415,6 +415,7 @@ cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
 }
 
 cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s) {
+  if (p.N == 128) return launch_fft128_image_ws(p, d_volts, T, ws, p.d_part, p.d_part_auto, s);
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
@@ -431,6 +432,7 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
 
 cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                                 int* part_auto, cudaStream_t s) {
+  if (p.N == 128) return launch_fft128_image_ws(p, d_volts, T, ws, part, part_auto, s);
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
   fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \

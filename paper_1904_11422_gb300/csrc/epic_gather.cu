@@ -3,7 +3,8 @@
 // The gridding of Eq. (5) (W * E') is done as a gather: every grid cell sums
 // w * e over the antennas whose kernel box covers it (the per-cell table built
 // by build_csr_kernel, antenna order).  An imaging kernel thread owns 8 cells
-// ("slots"); the 32 threads of a warp walk their k-th entries in lock step.
+// ("slots"), or 16 on 128 x 128 grids; the 32 threads of a warp walk their k-th
+// entries in lock step.
 // This file lays those entries out for that walk: for warp w and slot s the
 // trip count K_ws is the largest cell count among the warp's 32 cells (rounded
 // up to even for the FFT kernel, which walks entries two at a time to keep two
@@ -16,6 +17,8 @@
 // Cell layouts (thread task t, slot s -> cell (y, x)):
 //   kFft64: y = t / 8, x = t % 8 + 8 s   (the FFT kernel's row layout, N = 64)
 //   kFft32: y = t / 4, x = t % 4 + 4 s   (N = 32)
+//   kFft128: y = t / 8, x = t % 8 + 8 s, s < 16 (N = 128; 1024 tasks, the
+//            two CTAs of a cluster: tasks 512 r + i belong to CTA r)
 //   kChunk64: y = t / 8, x = 8 (t % 8) + s (eight consecutive cells)
 //   kPair64: four load-balanced cell pairs per thread (tensor path, see deal_pairs)
 // With sorting on, tasks are ordered by their number of entries (stable), so
@@ -29,7 +32,8 @@ namespace {
 
 __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
   switch (layout) {
-    case kLayoutFft64: return make_int2(task >> 3, (task & 7) + 8 * s);
+    case kLayoutFft64:
+    case kLayoutFft128: return make_int2(task >> 3, (task & 7) + 8 * s);
     case kLayoutFft32: return make_int2(task >> 2, (task & 3) + 4 * s);
     default: return make_int2(task >> 3, 8 * (task & 7) + s);
   }
@@ -67,16 +71,17 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
                                      float* __restrict__ ent_w) {
   extern __shared__ int sh[];
   const int nt = blockDim.x, warps = nt / 32;
-  int* kws = sh;                 // [warps * 8]
-  int* bws = kws + warps * 8;    // [warps * 8]
-  int* keys = bws + warps * 8;   // [nt], or [2048] for pairs
+  const int ns = layout == kLayoutFft128 ? 16 : 8;  // slots per thread
+  int* kws = sh;                 // [warps * ns]
+  int* bws = kws + warps * ns;   // [warps * ns]
+  int* keys = bws + warps * ns;  // [nt], or [2048] for pairs
   int* perm = keys + (layout == kLayoutPair64 ? 2048 : nt);   // [nt], or [2048]
   int* pair_of = perm + (layout == kLayoutPair64 ? 2048 : nt);  // [4 nt] (pairs only)
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int* ptr = csr_ptr + (size_t)c * (N * N + 1);
 
   int task = tid;
-  int2 cells[8];
+  int2 cells[16];
   if (layout == kLayoutPair64) {
     deal_pairs(ptr, tid, keys, perm, pair_of);
     for (int s = 0; s < 8; ++s) {
@@ -85,7 +90,7 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
     }
   } else {
     int key = 0;
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < ns; ++s) {
       const int2 yx = cell_of(layout, tid, s);
       key += ptr[yx.x * N + yx.y + 1] - ptr[yx.x * N + yx.y];
     }
@@ -98,22 +103,23 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
       __syncthreads();
       task = perm[tid];
     }
-    for (int s = 0; s < 8; ++s) cells[s] = cell_of(layout, task, s);
+    for (int s = 0; s < ns; ++s) cells[s] = cell_of(layout, task, s);
   }
-  int cnt[8], beg[8];
-  for (int s = 0; s < 8; ++s) {
+  int cnt[16], beg[16];
+  for (int s = 0; s < ns; ++s) {
     const int2 yx = cells[s];
     beg[s] = ptr[yx.x * N + yx.y];
     cnt[s] = ptr[yx.x * N + yx.y + 1] - beg[s];
     // FFT layouts: trip count rounded up to even (that kernel walks entries in pairs)
     const int kmax = __reduce_max_sync(0xffffffffu, cnt[s]);
-    const int k = (layout == kLayoutFft64 || layout == kLayoutFft32) ? ((kmax + 1) & ~1) : kmax;
-    if (lane == 0) kws[w * 8 + s] = k;
+    const int k = (layout == kLayoutFft64 || layout == kLayoutFft32 || layout == kLayoutFft128) ? ((kmax + 1) & ~1)
+                                                                                                : kmax;
+    if (lane == 0) kws[w * ns + s] = k;
   }
   __syncthreads();
   if (tid == 0) {
     int run = 0;
-    for (int q = 0; q < warps * 8; ++q) {
+    for (int q = 0; q < warps * ns; ++q) {
       bws[q] = run;
       run += 32 * kws[q];
     }
@@ -122,9 +128,9 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   __syncthreads();
   if (!fill) return;
   const size_t off = (size_t)chan_off[c];
-  if (tid < warps * 8) {
-    cnt_out[(size_t)c * warps * 8 + tid] = kws[tid];
-    base_out[(size_t)c * warps * 8 + tid] = bws[tid];
+  for (int q = tid; q < warps * ns; q += nt) {
+    cnt_out[(size_t)c * warps * ns + q] = kws[q];
+    base_out[(size_t)c * warps * ns + q] = bws[q];
   }
   if (layout == kLayoutPair64) {
     for (int j = 0; j < 4; ++j) task_out[((size_t)c * nt + tid) * 4 + j] = (uint16_t)pair_of[tid * 4 + j];
@@ -132,10 +138,10 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
     task_out[(size_t)c * nt + tid] = (uint16_t)task;
   }
   const int2* ent = csr_ent + (size_t)c * nnz;
-  for (int s = 0; s < 8; ++s) {
-    const int K = kws[w * 8 + s];
+  for (int s = 0; s < ns; ++s) {
+    const int K = kws[w * ns + s];
     for (int k = 0; k < K; ++k) {
-      const size_t idx = off + (size_t)bws[w * 8 + s] + 32 * k + lane;
+      const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
       if (k < cnt[s]) {
         const int2 e = ent[beg[s] + k];
         ent_a[idx] = (uint16_t)e.x;
@@ -156,8 +162,9 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   g.threads = threads;
   g.sorted = sorted;
   const int warps = threads / 32;
+  const int ns = layout == kLayoutFft128 ? 16 : 8;
   const int nnz = p.A * p.S * p.S;
-  const size_t smem = sizeof(int) * (2 * (size_t)warps * 8 +
+  const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
                                      (layout == kLayoutPair64 ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));
   int* d_tot = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * p.C);
@@ -183,8 +190,8 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
     return err;
   };
   if ((e = grab(reinterpret_cast<void**>(&g.d_chan_off), sizeof(int) * (p.C + 1))) != cudaSuccess) return e;
-  if ((e = grab(reinterpret_cast<void**>(&g.d_cnt), sizeof(int) * (size_t)p.C * warps * 8)) != cudaSuccess) return e;
-  if ((e = grab(reinterpret_cast<void**>(&g.d_base), sizeof(int) * (size_t)p.C * warps * 8)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_cnt), sizeof(int) * (size_t)p.C * warps * ns)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_base), sizeof(int) * (size_t)p.C * warps * ns)) != cudaSuccess) return e;
   const size_t per_thread = (layout == kLayoutPair64) ? 4 : 1;
   if ((e = grab(reinterpret_cast<void**>(&g.d_task), sizeof(uint16_t) * (size_t)p.C * threads * per_thread)) !=
       cudaSuccess)

@@ -39,12 +39,12 @@ struct WorkSplit {
 };
 
 // Gather tables of a gridder (see epic_gather.cu).
-enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3 };
+enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3, kLayoutFft128 = 4 };
 struct GatherTables {
   int layout = 0, threads = 0, sorted = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel
-  int* d_cnt = nullptr;          // [C][warps][8] trip count of (warp, slot)
-  int* d_base = nullptr;         // [C][warps][8] first entry of (warp, slot) within the channel
+  int* d_cnt = nullptr;          // [C][warps][slots] trip count of (warp, slot); 8 slots, 16 at N = 128
+  int* d_base = nullptr;         // [C][warps][slots] first entry of (warp, slot) within the channel
   int* d_chan_off = nullptr;     // [C+1] first entry of each channel
   uint16_t* d_task = nullptr;    // [C][threads] task of each thread ([C][threads][4] pairs for kLayoutPair64)
   uint16_t* d_ent_a = nullptr;   // [entries] antenna index (0 for padding)
@@ -129,6 +129,15 @@ void free_gather_tables(GatherTables& g);
 cudaError_t fft_image_config(Plan& p, int* ctas_per_sm);
 cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws,
                              cudaStream_t s);
+
+// The same path on 128 x 128 grids, run by clusters of two CTAs (epic_fft128.cu).
+// Sets p.threads, p.smem, p.ent_in_smem and returns the co-resident clusters;
+// an imaging launch's WorkSplit then counts clusters.
+size_t fft128_smem_need(int A, int P);
+int fft128_max_ant();
+cudaError_t fft128_config(Plan& p, int* clusters);
+cudaError_t launch_fft128_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
+                                   int* part_auto, cudaStream_t s);
 
 // Tensor-core path (DFT-by-GEMM on tcgen05; N = 64, two polarisations).
 size_t dft_smem_need(int A, int max_entries);

@@ -78,6 +78,8 @@ def test_validate_accepts_valid(lib):
     assert epic.epic_plan_validate(d) == epic.EPIC_OK
     d, keep = _desc(grid_n=64)
     assert epic.epic_plan_validate(d) == epic.EPIC_OK
+    d, keep = _desc(grid_n=128)
+    assert epic.epic_plan_validate(d) == epic.EPIC_OK
 
 
 @pytest.mark.parametrize("kw,code", [
@@ -85,7 +87,8 @@ def test_validate_accepts_valid(lib):
     (dict(kernel_support=17), epic.EPIC_ERR_INVALID_ARG),
     (dict(n_pol=3, gains=None, delays_s=None), epic.EPIC_ERR_INVALID_ARG),
     (dict(grid_n=48), epic.EPIC_ERR_INVALID_ARG),
-    (dict(grid_n=128), epic.EPIC_ERR_UNSUPPORTED),
+    (dict(grid_n=256), epic.EPIC_ERR_UNSUPPORTED),
+    (dict(grid_n=128, xform=1), epic.EPIC_ERR_UNSUPPORTED),
     (dict(cell_lambda=0.0), epic.EPIC_ERR_INVALID_ARG),
     (dict(kernel_sigma_cells=-1.0), epic.EPIC_ERR_INVALID_ARG),
     (dict(chan_freq_hz=[50e6, -1.0]), epic.EPIC_ERR_INVALID_ARG),
@@ -131,3 +134,15 @@ def test_validate_offgrid_agrees_with_oracle(lib):
 def test_no_cpu_fallback(tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         epic.load_library(str(tmp_path / "missing.so"))
+
+
+def test_validate_antenna_limits_per_grid(lib):
+    """The FP32 path takes up to 2048 antennas on 32 / 64 grids and up to 1024
+    on 128 x 128 grids (whose clusters keep every antenna's field in shared
+    memory next to half of the grid)."""
+    rng = np.random.default_rng(5)
+    for n_ant, grid_n, code in [(1024, 128, epic.EPIC_OK), (1025, 128, epic.EPIC_ERR_UNSUPPORTED),
+                                (2048, 64, epic.EPIC_OK), (2049, 64, epic.EPIC_ERR_UNSUPPORTED)]:
+        ant = (rng.random((n_ant, 2)) - 0.5) * 20.0  # within a few cells of the centre at 50 MHz
+        d, keep = epic.make_desc(ant, [50e6], 2, grid_n, 3)
+        assert epic.epic_plan_validate(d) == code, (n_ant, grid_n)

@@ -19,7 +19,8 @@ def lib():
 @pytest.fixture(scope="module")
 def arrays():
     return [synth.batching_array("A", n_time=300), synth.batching_array("B", n_time=300),
-            synth.random_small(1601, n_ant=40, n_pol=2, n_chan=7, grid_n=64, support=3, n_time=55)]
+            synth.random_small(1601, n_ant=40, n_pol=2, n_chan=7, grid_n=64, support=3, n_time=55),
+            synth.batching_array("C", n_time=60)]
 
 
 def _setup(ws, xforms):
@@ -43,7 +44,7 @@ def _single(plans, vols, ws):
 
 def test_batch_equals_single_calls_bit_for_bit(arrays):
     import torch
-    xforms = ["fft_fp32", "fft_fp32", "dft_bf16x3"]
+    xforms = ["fft_fp32", "fft_fp32", "dft_bf16x3", "fft_fp32"]
     plans, vols, outs = _setup(arrays, xforms)
     ref = _single(plans, vols, arrays)
     b = epic.epic_batch_create(plans, vols, [w.n_time for w in arrays], outs, tune=False)
@@ -61,7 +62,7 @@ def test_batch_equals_single_calls_bit_for_bit(arrays):
 
 def test_autotuned_batch_matches_oracle(arrays):
     import torch
-    xforms = ["fft_fp32", "fft_fp32", "fft_fp32"]
+    xforms = ["fft_fp32", "fft_fp32", "fft_fp32", "fft_fp32"]
     plans, vols, outs = _setup(arrays, xforms)
     ref = _single(plans, vols, arrays)
     b = epic.epic_batch_create(plans, vols, [w.n_time for w in arrays], outs, tune=True)
@@ -70,10 +71,10 @@ def test_autotuned_batch_matches_oracle(arrays):
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
         assert rel_errors(o.cpu().numpy(), r, 2).max() <= 1e-6
-    # array A against the oracle on two channels
-    got = outs[0].cpu().numpy()
-    chans = [0, 15]
-    assert_close(got[chans], oracle_image(arrays[0], channels=chans, use_fft=True), 2)
+    # arrays A and C against the oracle on two channels each
+    for k, chans in ((0, [0, 15]), (3, [0, 31])):
+        got = outs[k].cpu().numpy()
+        assert_close(got[chans], oracle_image(arrays[k], channels=chans, use_fft=True), 2)
     b.close()
     for p in plans:
         p.close()

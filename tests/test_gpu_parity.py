@@ -101,6 +101,10 @@ IMAGE_CASES = [
     dict(seed=203, n_ant=6, n_pol=2, n_chan=5, grid_n=64, support=1, n_time=3),
     dict(seed=204, n_ant=30, n_pol=2, n_chan=2, grid_n=64, support=3, n_time=40),
     dict(seed=205, n_ant=3, n_pol=1, n_chan=1, grid_n=32, support=5, n_time=1),
+    # 128 x 128 grids (clusters of two CTAs)
+    dict(seed=206, n_ant=24, n_pol=2, n_chan=3, grid_n=128, support=5, n_time=9),
+    dict(seed=207, n_ant=10, n_pol=1, n_chan=2, grid_n=128, support=3, n_time=5),
+    dict(seed=208, n_ant=70, n_pol=2, n_chan=5, grid_n=128, support=1, n_time=4),
 ]
 
 
@@ -258,3 +262,39 @@ def test_plans_coexist_after_a_smaller_plan(torch, station):
     assert_close(gpu_image(w, plan=small), oracle_image(w), 2)
     small.close()
     big.close()
+
+
+def test_grid128_largest_array(torch):
+    """1024 antennas on a 128 x 128 grid (the largest array the clusters take;
+    gather entries are read from L2 instead of shared memory)."""
+    w = synth.random_small(1801, n_ant=1024, n_pol=2, n_chan=2, grid_n=128, support=5, n_time=3)
+    plan = epic.plan_for(w)
+    assert plan.info["ctas"] >= 1
+    got = gpu_image(w, plan=plan)
+    assert_close(got, oracle_image(w), 2)
+    plan.close()
+
+
+def test_grid128_station_sampled_channels(torch):
+    """The station block on a 2x padded 128 x 128 grid (the precision study's
+    128^2 variant), full size in the benchmark's launch, channels 0, 40 and 63
+    against the oracle's FFT mode; the brightest source is where the recipe put
+    it, and the image is additive over time halves."""
+    w = synth.station(grid_n=128)
+    plan = epic.plan_for(w)
+    dv = torch.from_numpy(w.volts).cuda()
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    epic.epic_image(plan, dv, w.n_time, out, 0)
+    epic.epic_sync(plan)
+    gpu = out.cpu().numpy()
+    err = assert_close(gpu[[0, 40, 63]], oracle_image(w, channels=[0, 40, 63], use_fft=True), 2)
+    assert err.max() < TOL_FP32
+    xx = gpu[:, 0].sum(0)
+    i, j, _ = w.sources[0]
+    assert np.unravel_index(np.argmax(xx), xx.shape) == (j, i)
+    h = torch.empty_like(out)
+    epic.epic_image(plan, dv[:600].contiguous(), 600, h, 0)
+    epic.epic_image(plan, dv[600:].contiguous(), w.n_time - 600, h, 1)
+    epic.epic_sync(plan)
+    assert rel_errors(h.cpu().numpy(), gpu, 2).max() < 2e-6
+    plan.close()
