@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--soak-seconds", type=float, default=1.5)
+    ap.add_argument("--grid128-steps", type=int, default=20,
+                    help="calls timed on the station block at 128 x 128 (0 to skip)")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="graph launches timed for the batching workload (0 to skip)")
     ap.add_argument("--grad-steps", type=int, default=20,
@@ -233,6 +235,47 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def time_grid128(args, epic, synth, torch, stream, world, shard, sms, pk, pk_kind):
+    """The station block imaged on a 2x padded 128 x 128 grid (FP32 path, clusters
+    of two CTAs), with its kernel's fraction of the FP32 peak."""
+    w = synth.station(grid_n=128)
+    plan = epic.plan_for(w)
+    dv = [torch.from_numpy(w.volts).cuda() for _ in range(2)]
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    for i in range(3):
+        epic.epic_image(plan, dv[i % 2], w.n_time, out, 0, stream)
+    torch.cuda.synchronize()
+    epic.epic_timing_enable(plan, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.grid128_steps):
+        epic.epic_image(plan, dv[i % 2], w.n_time, out, 0, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.grid128_steps, device="cuda")
+    kt = epic.epic_timing_read(plan)
+    epic.epic_timing_enable(plan, False)
+    epic.epic_sync(plan)
+    n, tot = kt["fft_image"]
+    avg_s = tot / n / 1e3
+    flops = w.n_chan * w.n_time * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
+    peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    res = {"workload": "station block (256 dual-pol antennas, 64 channels, 1250 samples, 5x5) on a 2x padded "
+                       "128x128 grid", "xform": "fft_fp32", "error_bound": ERROR_BOUND["fft_fp32"],
+           "ms_per_call": ms, "value": w.units * world / (ms / 1e3), "unit": UNIT,
+           "roofline": {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": flops / avg_s / 1e12 / peak, "kernel": "fft_image (N = 128, 2-CTA clusters)",
+                        "kernel_ms": 1e3 * avg_s, "flops_per_launch": flops,
+                        "traffic": dram_traffic("fft128_image", "epic_fft128.cu"),
+                        "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
+                                      f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind})"},
+           "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kt.items()},
+           "clusters": plan.info["ctas"]}
+    plan.close()
+    return res
+
+
 def time_batch(args, epic, synth, torch, stream, world, shard):
     """Arrays A, B and C of the batching recipe (T = 1250 each), every plan that
     the library supports in one autotuned graph; also the same plans imaged by
@@ -442,6 +485,11 @@ def main():
         gplan.close()
         splan.close()
 
+    # the precision study's 128 x 128 variant of the station block
+    grid128 = None
+    if args.grid128_steps > 0:
+        grid128 = time_grid128(args, epic, synth, torch, stream, world, shard, sms, pk, pk_kind)
+
     # batching: the arrays of the batching recipe imaged by one graph launch
     batch = None
     if args.batch_steps > 0:
@@ -466,7 +514,8 @@ def main():
                                  f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
                 "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": primary["gpu_launches"], "kernel_times_ms": primary["kernel_times_ms"],
-                "paths": others, "grad": grad, "batch": batch, "clocks": clocks}
+                "paths": others, "grad": grad, "grid128": grid128, "batch": batch,
+                "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
