@@ -313,7 +313,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
 
     // 2. grid (gather, fixed order) and 3a. row transforms; thread (local row
-    //    `line`, n1) owns cells (64 rank + line, n1 + 8 n2)
+    //    `line`, n1) owns cells (64 rank + line, n1 + 8 n2).  A warp whose four
+    //    rows hold no entries (outside the aperture of a padded grid) skips its
+    //    transforms: the transform of a zero line is zero.
+    int any = 0;
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) any |= cnt_s[warp * kSlots + q];
     {
       float2 v[P][16];
 #pragma unroll
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         float2* row = Rbuf + (size_t)(p * kRows + line) * kN;
-        fft_line128(v[p], tw_s, row, line, n1);
+        if (any) fft_line128(v[p], tw_s, row, line, n1);
 #pragma unroll
         for (int s = 0; s < 16; ++s) row[cpos(line, kidx(n1, s))] = v[p][s];
       }
