@@ -31,10 +31,10 @@ bool grid_supported(int xform, int N, int P, int A, int S) {
     if (N == 128) return A <= epic::fft128_max_ant() && epic::fft128_smem_need(A, P) <= kSmemOptin;
     return (N == 32 || N == 64) && A <= kMaxAntFft;
   }
-  // tensor path: 64 x 64 grids of two polarisations, with the gather entries in
-  // shared memory (bounded here by the unpadded count A S^2; the exact padded
-  // count is checked when the plan is created)
-  return N == 64 && P == 2 && A <= 512 && epic::dft_smem_need(A, A * S * S) <= kSmemOptin;
+  // tensor path: 64 x 64 or 128 x 128 grids of two polarisations, up to 1024
+  // antennas (gather entries in shared memory when they fit, else read from L2)
+  (void)S;
+  return (N == 64 || N == 128) && P == 2 && A <= 1024 && epic::dft_smem_need(A, 0) <= kSmemOptin;
 }
 
 epic_status from_cuda(cudaError_t e) {
@@ -135,7 +135,7 @@ int spans_needed(const epic::WorkSplit& ws) {
 epic::WorkSplit split_work_cap(const Plan& p, int T, int cap) {
   epic::WorkSplit ws;
   ws.T = T;
-  ws.units = (long long)p.C * T;
+  ws.units = (long long)p.C * p.vq * T;
   long long ctas = cap < ws.units ? cap : ws.units;
   ws.W = (ws.units + ctas - 1) / ctas;
   ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);
@@ -308,13 +308,10 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
     total += gt_bytes;
     EPIC_TRY(epic::fft_image_config(p, &per_sm));
   } else {
-    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutPair64, 512, 0, &gt_bytes));
+    // N = 128: four virtual channels per channel, one per output-parity subset
+    p.vq = p.N == 128 ? 4 : 1;
+    EPIC_TRY(epic::build_gather_tables(p, p.N == 128 ? epic::kLayoutPairQ : epic::kLayoutPair64, 512, 0, &gt_bytes));
     total += gt_bytes;
-    if (epic::dft_smem_need(p.A, p.gt.max_chan_entries) > kSmemOptin) {
-      free_plan(p);
-      delete h;
-      return EPIC_ERR_UNSUPPORTED;  // the padded gather table does not fit in shared memory
-    }
     EPIC_TRY(alloc(&p.d_fmat, (size_t)4 * 128 * 128 / 2, &total));
     EPIC_TRY(epic::launch_dft_tables(p, 0));
     EPIC_TRY(cudaDeviceSynchronize());
@@ -322,9 +319,10 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   }
   if (clusters == 0 && per_sm < 1) return fail(cudaErrorInvalidConfiguration);
   p.ctas = clusters > 0 ? clusters : p.sm_count * per_sm;
-  p.spans = (p.C + p.ctas - 1) / p.ctas + 2;
+  p.spans = (p.C * p.vq + p.ctas - 1) / p.ctas + 2;
   size_t before = total;
-  EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * N * N, &total));
+  const size_t Ns = p.vq == 4 ? N / 2 : N;  // side of a partial image
+  EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * Ns * Ns, &total));
   EPIC_TRY(alloc(&p.d_part_auto, (size_t)p.ctas * p.spans * A * 4, &total));
   p.workspace_bytes = total - before;
   // epic_grad: FP32 FFT plans of 64 x 64 grids with one antenna per thread

@@ -97,7 +97,7 @@ bool cap_fits(const epic::Plan& p, int T, int cap) {
   if (T == 0) return true;
   epic::WorkSplit ws;
   ws.T = T;
-  ws.units = (long long)p.C * T;
+  ws.units = (long long)p.C * p.vq * T;
   const long long ctas = cap < ws.units ? cap : ws.units;
   ws.W = (ws.units + ctas - 1) / ctas;
   ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);

@@ -167,14 +167,24 @@ struct DftSmem {
   static constexpr uint32_t E = 8 * kSlab;   // [A] float4 calibrated fields, then coefficients, self powers, entries
 };
 
-template <int XF>
+// Q128: a 128 x 128 grid, transformed as four 64 x 64 problems.  With the
+// output pixel (row 2 j + beta, column 2 k + alpha), one radix-2 step along each
+// axis gives Y_128[2j+beta][2k+alpha] = (F_64 H_q F_64^T)[j][k] for
+//   H_q[y][x] = exp(+2 pi i (alpha x + beta y) / 128)
+//               sum_{u,s in {0,1}} (-1)^(alpha s + beta u) G[y + 64 u][x + 64 s],
+// q = alpha + 2 beta.  The kernel runs virtual channels 4 c + q: the gather
+// tables of virtual channel 4 c + q fold the four quadrants with signed weights
+// (layout kLayoutPairQ), the twiddle is applied to each gathered cell, and the
+// rest of the path is the 64 x 64 transform; the reduction interleaves the four
+// sub-images.
+template <int XF, bool Q128>
 __global__ void __launch_bounds__(kThreads, 1)
     dft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
                      const int* __restrict__ g_off, const uint16_t* __restrict__ g_task,
                      const uint16_t* __restrict__ g_ent_a, const float* __restrict__ g_ent_w, int max_entries,
-                     const uint32_t* __restrict__ fmat, float* __restrict__ part, int* __restrict__ part_auto,
-                     int* __restrict__ status) {
+                     int ent_in_smem, const uint32_t* __restrict__ fmat, const float2* __restrict__ twiddle,
+                     float* __restrict__ part, int* __restrict__ part_auto, int* __restrict__ status) {
   using Pr = Prec<XF>;
   constexpr bool kBf = Pr::kBf16;
   constexpr int NN = kN * kN;
@@ -186,7 +196,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float4* E4 = reinterpret_cast<float4*>(sm + DftSmem::E);
   float2* coef_s = reinterpret_cast<float2*>(E4 + A);       // [A][2]
   int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A);    // [A]
-  int* cnt_s = reinterpret_cast<int*>(auto_s + A);           // [16 warps][8] trip counts
+  float2* tw_s = reinterpret_cast<float2*>(auto_s + A);      // [128] exp(+2 pi i m / 128) (Q128)
+  int* cnt_s = reinterpret_cast<int*>(tw_s + 128);           // [16 warps][8] trip counts
   int* base_s = cnt_s + 16 * 8;                              // [16 warps][8] first entries
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(base_s + 16 * 8);  // stage 1, stage 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -200,6 +211,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (u0 >= u1) return;
   const int c_first = (int)(u0 / T);
   const uint32_t bar1 = smem_u32(&bars[0]), bar2 = smem_u32(&bars[1]);
+  if constexpr (Q128)
+    for (int m = tid; m < 128; m += kThreads) tw_s[m] = twiddle[m];
 
   // ---- set-up: TMEM, mbarriers, the DFT matrix into TMEM ----
   if (warp == 0) {
@@ -293,14 +306,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int a = tid; a < A; a += kThreads) pa[a] = auto_s[a];
   };
 
-  // the two bytes of the thread's antenna (a = tid < A <= 512), prefetched one
-  // sample ahead so that the unpack never waits for HBM
+  // the two bytes of each of the thread's antennas (a = tid + 512 k < A <= 1024),
+  // prefetched one sample ahead so that the unpack never waits for HBM; packed
+  // as antenna tid in the low and antenna tid + 512 in the high half
   auto load_raw = [&](long long u) -> unsigned {
     const int c = (int)(u / T), t = (int)(u % T);
-    const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * 2;
-    return tid < A ? (unsigned)__ldg(reinterpret_cast<const unsigned short*>(base) + tid) : 0u;
+    const int cr = Q128 ? c >> 2 : c;
+    const unsigned short* base = reinterpret_cast<const unsigned short*>(volts + ((size_t)t * C + cr) * (size_t)A * 2);
+    unsigned r = tid < A ? (unsigned)__ldg(base + tid) : 0u;
+    if (tid + kThreads < A) r |= (unsigned)__ldg(base + tid + kThreads) << 16;
+    return r;
   };
   unsigned raw = load_raw(u0), raw_next = 0;
+  const uint16_t* ent_a = enta_s;
+  const float* ent_w = entw_s;
 
   int cur_c = -1;
   for (long long u = u0; u < u1; ++u) {
@@ -321,16 +340,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       cur_c = c;
       tc_fence_before();
       __syncthreads();
-      for (int k = tid; k < 2 * A; k += kThreads) coef_s[k] = coef[(size_t)c * A * 2 + k];
+      const int cr = Q128 ? c >> 2 : c;
+      for (int k = tid; k < 2 * A; k += kThreads) coef_s[k] = coef[(size_t)cr * A * 2 + k];
       for (int a = tid; a < A; a += kThreads) auto_s[a] = make_int4(0, 0, 0, 0);
       if (tid < 16 * 8) {
         cnt_s[tid] = g_cnt[(size_t)c * 16 * 8 + tid];
         base_s[tid] = g_base[(size_t)c * 16 * 8 + tid];
       }
       const int e0 = g_off[c], ne = g_off[c + 1] - e0;
-      for (int k = tid; k < ne; k += kThreads) {
-        enta_s[k] = g_ent_a[e0 + k];
-        entw_s[k] = g_ent_w[e0 + k];
+      if (ent_in_smem) {
+        for (int k = tid; k < ne; k += kThreads) {
+          enta_s[k] = g_ent_a[e0 + k];
+          entw_s[k] = g_ent_w[e0 + k];
+        }
+        ent_a = enta_s;
+        ent_w = entw_s;
+      } else {
+        ent_a = g_ent_a + e0;
+        ent_w = g_ent_w + e0;
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) pair[j] = g_task[((size_t)c * kThreads + tid) * 4 + j];
@@ -340,11 +367,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (u + 1 < u1) raw_next = load_raw(u + 1);
 
     // 1. unpack, calibrate, exact integer self powers
-    {
-      const int a = tid;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = tid + h * kThreads;
+      const unsigned rb = h ? raw >> 16 : raw & 0xffffu;
       if (a < A) {
-        const int xr = nib_hi(raw & 0xffu), xi = nib_lo(raw & 0xffu);
-        const int yr = nib_hi(raw >> 8), yi = nib_lo(raw >> 8);
+        const int xr = nib_hi(rb & 0xffu), xi = nib_lo(rb & 0xffu);
+        const int yr = nib_hi(rb >> 8), yi = nib_lo(rb >> 8);
         const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
         E4[a] = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
                             ky.x * yi + ky.y * yr);
@@ -371,14 +400,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = base_s[warp * 8 + s] + lane;
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
         for (int k = 0; k < K; ++k) {
-          const float w = entw_s[b + 32 * k];
-          const float4 ev = E4[enta_s[b + 32 * k]];
+          const float w = ent_w[b + 32 * k];
+          const float4 ev = E4[ent_a[b + 32 * k]];
           xr = fmaf(w, ev.x, xr);
           xi = fmaf(w, ev.y, xi);
           yr = fmaf(w, ev.z, yr);
           yi = fmaf(w, ev.w, yi);
         }
         gre[0][s] = xr; gim[0][s] = xi; gre[1][s] = yr; gim[1][s] = yi;
+      }
+      if constexpr (Q128) {
+        // H_q = exp(+2 pi i (alpha x + beta y) / 128) x the folded gather
+        const int alpha = cur_c & 1, beta = (cur_c >> 1) & 1;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int y = pair[s >> 1] >> 5, x = 2 * (pair[s >> 1] & 31) + (s & 1);
+          const float2 w = tw_s[(alpha * x + beta * y) & 127];
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            const float re = gre[g][s], im = gim[g][s];
+            gre[g][s] = re * w.x - im * w.y;
+            gim[g][s] = re * w.y + im * w.x;
+          }
+        }
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -539,6 +583,7 @@ __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
 size_t dft_smem_bytes(int A, int max_entries) {
   size_t b = 8 * (size_t)kSlab;            // the two B operands (gridded fields, stage-1 result)
   b += 16 * (size_t)A + 16 * (size_t)A + 16 * (size_t)A;  // E, coefficients, self powers
+  b += 128 * sizeof(float2);                // twiddles of the 128 x 128 split
   b += 2 * 16 * 8 * sizeof(int);            // gather trip counts and bases
   b += 32;                                  // two mbarriers, TMEM address, abort flag
   b += 6 * (size_t)max_entries;             // gather entries (weight, antenna)
@@ -548,16 +593,20 @@ size_t dft_smem_bytes(int A, int max_entries) {
 template <int XF>
 cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                        int* part_auto, cudaStream_t s) {
-  dft_image_kernel<XF><<<ws.ctas, kThreads, p.smem, s>>>(
-      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-      p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, reinterpret_cast<const uint32_t*>(p.d_fmat),
-      part, part_auto, p.d_status);
+  auto kern = p.N == 128 ? dft_image_kernel<XF, true> : dft_image_kernel<XF, false>;
+  kern<<<ws.ctas, kThreads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt,
+                                         p.gt.d_base, p.gt.d_chan_off, p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w,
+                                         p.gt.max_chan_entries, p.ent_in_smem,
+                                         reinterpret_cast<const uint32_t*>(p.d_fmat), p.d_twiddle, part, part_auto,
+                                         p.d_status);
   return cudaGetLastError();
 }
 
 template <int XF>
 cudaError_t dft_attr() {
-  return allow_max_smem(dft_image_kernel<XF>);
+  cudaError_t e = allow_max_smem(dft_image_kernel<XF, false>);
+  if (e == cudaSuccess) e = allow_max_smem(dft_image_kernel<XF, true>);
+  return e;
 }
 
 }  // namespace
@@ -575,9 +624,15 @@ cudaError_t launch_dft_tables(Plan& p, cudaStream_t s) {
 }
 
 cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
+  int dev = 0, optin = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e0 != cudaSuccess) return e0;
   p.threads = kThreads;
-  p.smem = dft_smem_bytes(p.A, p.gt.max_chan_entries);
-  p.ent_in_smem = 1;
+  // gather entries in shared memory when they fit, else read through L1/L2
+  p.ent_in_smem = dft_smem_bytes(p.A, p.gt.max_chan_entries) <= (size_t)optin ? 1 : 0;
+  p.smem = dft_smem_bytes(p.A, p.ent_in_smem ? p.gt.max_chan_entries : 0);
+  if (p.smem > (size_t)optin) return cudaErrorInvalidConfiguration;
   cudaError_t e;
   switch (p.xform) {
     case EPIC_XFORM_DFT_BF16X3: e = dft_attr<EPIC_XFORM_DFT_BF16X3>(); break;

@@ -21,6 +21,12 @@
 //            two CTAs of a cluster: tasks 512 r + i belong to CTA r)
 //   kChunk64: y = t / 8, x = 8 (t % 8) + s (eight consecutive cells)
 //   kPair64: four load-balanced cell pairs per thread (tensor path, see deal_pairs)
+//   kPairQ: the same over the 64 x 64 field H_q that the tensor path transforms
+//           for output-parity subset q of a 128 x 128 grid: H_q(y, x) sums the
+//           four grid cells (y + 64 u, x + 64 s), u, s in {0, 1}, with sign
+//           (-1)^(alpha s + beta u) (alpha = q & 1, beta = q >> 1); its entry
+//           list is the four cells' lists in (u, s) order, weights signed.  One
+//           table set per virtual channel 4 c + q.
 // With sorting on, tasks are ordered by their number of entries (stable), so
 // warps get cells of similar load; thread i of a channel then works on task
 // task[i].
@@ -39,16 +45,28 @@ __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
   }
 }
 
-// kLayoutPair64: the 2048 cell pairs (y, 2r..2r+1) of a 64 x 64 grid, ranked by
-// their number of entries (descending, ties by index) and dealt to the 512
-// threads in snake order, four per thread: thread t gets the pairs of rank
-// j*512 + t (j even) or j*512 + 511 - t (j odd), j = 0..3, so every thread's
+// Entries of cell (y, x) of the gathered field: a grid cell, or for kLayoutPairQ
+// the four grid cells folded into H_q(y, x).
+__device__ __forceinline__ int field_count(int layout, const int* ptr, int N, int y, int x) {
+  if (layout != kLayoutPairQ) return ptr[y * N + x + 1] - ptr[y * N + x];
+  int n = 0;
+  for (int us = 0; us < 4; ++us) {
+    const int cell = (y + 64 * (us >> 1)) * N + x + 64 * (us & 1);
+    n += ptr[cell + 1] - ptr[cell];
+  }
+  return n;
+}
+
+// kLayoutPair64 / kLayoutPairQ: the 2048 cell pairs (y, 2r..2r+1) of a 64 x 64
+// field, ranked by their number of entries (descending, ties by index) and dealt
+// to the 512 threads in snake order, four per thread: thread t gets the pairs of
+// rank j*512 + t (j even) or j*512 + 511 - t (j odd), j = 0..3, so every thread's
 // total is close to the mean.  Slot s of the thread is cell (s & 1) of its pair
 // s >> 1.  pair_of[t*4 + j] receives pair index y*32 + r.
-__device__ void deal_pairs(const int* ptr, int tid, int* loads, int* perm, int* pair_of) {
+__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int* loads, int* perm, int* pair_of) {
   for (int q = tid; q < 2048; q += 512) {
-    const int y = q >> 5, r = q & 31, cell = y * 64 + 2 * r;
-    loads[q] = ptr[cell + 2] - ptr[cell];
+    const int y = q >> 5, r = q & 31;
+    loads[q] = field_count(layout, ptr, N, y, 2 * r) + field_count(layout, ptr, N, y, 2 * r + 1);
   }
   __syncthreads();
   for (int q = tid; q < 2048; q += 512) {
@@ -74,16 +92,20 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   const int ns = layout == kLayoutFft128 ? 16 : 8;  // slots per thread
   int* kws = sh;                 // [warps * ns]
   int* bws = kws + warps * ns;   // [warps * ns]
+  const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ;
   int* keys = bws + warps * ns;  // [nt], or [2048] for pairs
-  int* perm = keys + (layout == kLayoutPair64 ? 2048 : nt);   // [nt], or [2048]
-  int* pair_of = perm + (layout == kLayoutPair64 ? 2048 : nt);  // [4 nt] (pairs only)
+  int* perm = keys + (pairs ? 2048 : nt);     // [nt], or [2048]
+  int* pair_of = perm + (pairs ? 2048 : nt);  // [4 nt] (pairs only)
+  // table set (channel, or virtual channel 4 c + q) and the grid channel it reads
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int* ptr = csr_ptr + (size_t)c * (N * N + 1);
+  const int cg = layout == kLayoutPairQ ? c >> 2 : c;
+  const int alpha = c & 1, beta = (c >> 1) & 1;  // kLayoutPairQ only
+  const int* ptr = csr_ptr + (size_t)cg * (N * N + 1);
 
   int task = tid;
   int2 cells[16];
-  if (layout == kLayoutPair64) {
-    deal_pairs(ptr, tid, keys, perm, pair_of);
+  if (pairs) {
+    deal_pairs(layout, ptr, N, tid, keys, perm, pair_of);
     for (int s = 0; s < 8; ++s) {
       const int q = pair_of[tid * 4 + (s >> 1)];
       cells[s] = make_int2(q >> 5, 2 * (q & 31) + (s & 1));
@@ -108,8 +130,8 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   int cnt[16], beg[16];
   for (int s = 0; s < ns; ++s) {
     const int2 yx = cells[s];
-    beg[s] = ptr[yx.x * N + yx.y];
-    cnt[s] = ptr[yx.x * N + yx.y + 1] - beg[s];
+    beg[s] = layout == kLayoutPairQ ? 0 : ptr[yx.x * N + yx.y];
+    cnt[s] = field_count(layout, ptr, N, yx.x, yx.y);
     // FFT layouts: trip count rounded up to even (that kernel walks entries in pairs)
     const int kmax = __reduce_max_sync(0xffffffffu, cnt[s]);
     const int k = (layout == kLayoutFft64 || layout == kLayoutFft32 || layout == kLayoutFft128) ? ((kmax + 1) & ~1)
@@ -132,14 +154,36 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
     cnt_out[(size_t)c * warps * ns + q] = kws[q];
     base_out[(size_t)c * warps * ns + q] = bws[q];
   }
-  if (layout == kLayoutPair64) {
+  if (pairs) {
     for (int j = 0; j < 4; ++j) task_out[((size_t)c * nt + tid) * 4 + j] = (uint16_t)pair_of[tid * 4 + j];
   } else {
     task_out[(size_t)c * nt + tid] = (uint16_t)task;
   }
-  const int2* ent = csr_ent + (size_t)c * nnz;
+  const int2* ent = csr_ent + (size_t)cg * nnz;
   for (int s = 0; s < ns; ++s) {
     const int K = kws[w * ns + s];
+    if (layout == kLayoutPairQ) {
+      // the four source cells' entries in (u, s) order, weights signed, then padding
+      int k = 0;
+      for (int us = 0; us < 4; ++us) {
+        const int u = us >> 1, sx = us & 1;
+        const int cell = (cells[s].x + 64 * u) * N + cells[s].y + 64 * sx;
+        const int b0 = ptr[cell], n = ptr[cell + 1] - b0;
+        const bool neg = ((alpha * sx + beta * u) & 1) != 0;
+        for (int i = 0; i < n; ++i, ++k) {
+          const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
+          const int2 e = ent[b0 + i];
+          ent_a[idx] = (uint16_t)e.x;
+          ent_w[idx] = neg ? -__int_as_float(e.y) : __int_as_float(e.y);
+        }
+      }
+      for (; k < K; ++k) {
+        const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
+        ent_a[idx] = 0;
+        ent_w[idx] = 0.f;
+      }
+      continue;
+    }
     for (int k = 0; k < K; ++k) {
       const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
       if (k < cnt[s]) {
@@ -164,43 +208,45 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   const int warps = threads / 32;
   const int ns = layout == kLayoutFft128 ? 16 : 8;
   const int nnz = p.A * p.S * p.S;
+  const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ;
+  const int nsets = layout == kLayoutPairQ ? 4 * p.C : p.C;  // table sets (virtual channels)
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
-                                     (layout == kLayoutPair64 ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));
+                                     (pairs ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));
   int* d_tot = nullptr;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * p.C);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * nsets);
   if (e != cudaSuccess) return e;
-  gather_tables_kernel<<<p.C, threads, smem>>>(layout, p.N, nnz, sorted, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, sorted, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
                                                nullptr, nullptr, nullptr, nullptr, nullptr);
   e = cudaGetLastError();
-  std::vector<int> tot(p.C);
-  if (e == cudaSuccess) e = cudaMemcpy(tot.data(), d_tot, sizeof(int) * p.C, cudaMemcpyDeviceToHost);
+  std::vector<int> tot(nsets);
+  if (e == cudaSuccess) e = cudaMemcpy(tot.data(), d_tot, sizeof(int) * nsets, cudaMemcpyDeviceToHost);
   cudaFree(d_tot);
   if (e != cudaSuccess) return e;
-  std::vector<int> off(p.C + 1, 0);
+  std::vector<int> off(nsets + 1, 0);
   g.max_chan_entries = 0;
-  for (int c = 0; c < p.C; ++c) {
+  for (int c = 0; c < nsets; ++c) {
     off[c + 1] = off[c] + tot[c];
     if (tot[c] > g.max_chan_entries) g.max_chan_entries = tot[c];
   }
-  const size_t total = (size_t)off[p.C];
+  const size_t total = (size_t)off[nsets];
   size_t bytes = 0;
   auto grab = [&](void** ptr, size_t b) {
     cudaError_t err = cudaMalloc(ptr, b > 0 ? b : 16);
     if (err == cudaSuccess) bytes += b;
     return err;
   };
-  if ((e = grab(reinterpret_cast<void**>(&g.d_chan_off), sizeof(int) * (p.C + 1))) != cudaSuccess) return e;
-  if ((e = grab(reinterpret_cast<void**>(&g.d_cnt), sizeof(int) * (size_t)p.C * warps * ns)) != cudaSuccess) return e;
-  if ((e = grab(reinterpret_cast<void**>(&g.d_base), sizeof(int) * (size_t)p.C * warps * ns)) != cudaSuccess) return e;
-  const size_t per_thread = (layout == kLayoutPair64) ? 4 : 1;
-  if ((e = grab(reinterpret_cast<void**>(&g.d_task), sizeof(uint16_t) * (size_t)p.C * threads * per_thread)) !=
+  if ((e = grab(reinterpret_cast<void**>(&g.d_chan_off), sizeof(int) * (nsets + 1))) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_cnt), sizeof(int) * (size_t)nsets * warps * ns)) != cudaSuccess) return e;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_base), sizeof(int) * (size_t)nsets * warps * ns)) != cudaSuccess) return e;
+  const size_t per_thread = pairs ? 4 : 1;
+  if ((e = grab(reinterpret_cast<void**>(&g.d_task), sizeof(uint16_t) * (size_t)nsets * threads * per_thread)) !=
       cudaSuccess)
     return e;
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_a), sizeof(uint16_t) * total)) != cudaSuccess) return e;
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_w), sizeof(float) * total)) != cudaSuccess) return e;
-  if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (p.C + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (nsets + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
-  gather_tables_kernel<<<p.C, threads, smem>>>(layout, p.N, nnz, sorted, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, sorted, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
                                                nullptr, g.d_cnt, g.d_base, g.d_task, g.d_ent_a, g.d_ent_w);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -39,7 +39,8 @@ struct WorkSplit {
 };
 
 // Gather tables of a gridder (see epic_gather.cu).
-enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3, kLayoutFft128 = 4 };
+enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3, kLayoutFft128 = 4,
+             kLayoutPairQ = 5 };
 struct GatherTables {
   int layout = 0, threads = 0, sorted = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel
@@ -54,6 +55,7 @@ struct GatherTables {
 struct Plan {
   // descriptor copy
   int A, P, C, N, S, xform, subtract;
+  int vq = 1;  // virtual channels per channel: 4 for the tensor path at N = 128 (output-parity subsets)
   double cell_lambda, sigma;
   int device, sm_count;
 

@@ -14,26 +14,35 @@ namespace {
 
 constexpr int kReduceThreads = 256;
 
+// One block per (channel, `rows` rows).  With vq = 4 (the tensor path on
+// 128 x 128 grids) the partials are the 64 x 64 sub-images of virtual channels
+// 4 c + q, and pixel (j, i) of sub-image q lands on output pixel
+// (2 j + beta, 2 i + alpha), alpha = q & 1, beta = q >> 1.
 template <int P>
 __global__ void __launch_bounds__(kReduceThreads)
-    reduce_kernel(int T, int C, int A, int N, long long W, int ctas, int spans, int subtract, int accumulate,
+    reduce_kernel(int T, int C, int A, int N, int vq, long long W, int ctas, int spans, int subtract, int accumulate,
                   int rows, const float* __restrict__ part, const int* __restrict__ part_auto,
                   const double2* __restrict__ coef64, const float* __restrict__ kx2, const float* __restrict__ ky2,
                   float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* Pw = reinterpret_cast<float4*>(smem);        // [A] self powers XX, YY, Re XY, Im XY
   float* kys = reinterpret_cast<float*>(Pw + A);       // [A][rows] |FT w_y|^2 of this block's rows
-  const int c = blockIdx.x;
+  const int cv = blockIdx.x;                           // (virtual) channel of the partials
+  const int c = vq == 4 ? cv >> 2 : cv;                // output channel
+  const int alpha = vq == 4 ? (cv & 1) : 0, beta = vq == 4 ? (cv >> 1) & 1 : 0;
+  const int Ns = vq == 4 ? N / 2 : N;                  // side of a partial image
   const int j0 = blockIdx.y * rows;
-  const int NN = N * N;
-  const long long b_lo = ((long long)c * T) / W;
-  const long long b_hi = min(((long long)(c + 1) * T - 1) / W, (long long)ctas - 1);
+  const int NN = N * N, NNs = Ns * Ns;
+  auto orow = [&](int j) { return vq == 4 ? 2 * j + beta : j; };
+  auto ocol = [&](int i) { return vq == 4 ? 2 * i + alpha : i; };
+  const long long b_lo = ((long long)cv * T) / W;
+  const long long b_hi = min(((long long)(cv + 1) * T - 1) / W, (long long)ctas - 1);
 
   if (subtract) {
     for (int a = threadIdx.x; a < A; a += blockDim.x) {
       long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
       for (long long b = b_lo; b <= b_hi; ++b) {
-        const int slot = c - (int)((b * W) / T);
+        const int slot = cv - (int)((b * W) / T);
         const int4 v = reinterpret_cast<const int4*>(part_auto)[(b * spans + slot) * A + a];
         s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
       }
@@ -47,27 +56,28 @@ __global__ void __launch_bounds__(kReduceThreads)
         pw.w = (float)(mr * (double)s3 + mi * (double)s2);
       }
       Pw[a] = pw;
-      for (int jj = 0; jj < rows; ++jj) kys[a * rows + jj] = ky2[((size_t)c * A + a) * N + j0 + jj];
+      for (int jj = 0; jj < rows; ++jj) kys[a * rows + jj] = ky2[((size_t)c * A + a) * N + orow(j0 + jj)];
     }
     __syncthreads();
   }
 
-  for (int q = threadIdx.x; q < rows * N; q += blockDim.x) {
-    const int jj = q / N, i = q % N, pix = (j0 + jj) * N + i;
+  for (int q = threadIdx.x; q < rows * Ns; q += blockDim.x) {
+    const int jj = q / Ns, i = q % Ns, pix = (j0 + jj) * Ns + i;
+    const int opix = orow(j0 + jj) * N + ocol(i);
     float s[4] = {0.f, 0.f, 0.f, 0.f};
     for (long long b = b_lo; b <= b_hi; ++b) {
-      const int slot = c - (int)((b * W) / T);
-      const float* src = part + (size_t)(b * spans + slot) * 4 * NN + pix;
+      const int slot = cv - (int)((b * W) / T);
+      const float* src = part + (size_t)(b * spans + slot) * 4 * NNs + pix;
       s[0] += src[0];
       if (P == 2) {
-        s[1] += src[NN];
-        s[2] += src[2 * NN];
-        s[3] += src[3 * NN];
+        s[1] += src[NNs];
+        s[2] += src[2 * NNs];
+        s[3] += src[3 * NNs];
       }
     }
     if (subtract) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      const float* kxc = kx2 + (size_t)c * A * N + i;
+      const float* kxc = kx2 + (size_t)c * A * N + ocol(i);
       for (int a = 0; a < A; ++a) {
         const float w2 = kxc[(size_t)a * N] * kys[a * rows + jj];
         const float4 pw = Pw[a];
@@ -80,7 +90,7 @@ __global__ void __launch_bounds__(kReduceThreads)
       }
       s[0] -= a0; s[1] -= a1; s[2] -= a2; s[3] -= a3;
     }
-    float* o = out + (size_t)c * 4 * NN + pix;
+    float* o = out + (size_t)c * 4 * NN + opix;
 #pragma unroll
     for (int pl = 0; pl < 4; ++pl) o[pl * NN] = accumulate ? o[pl * NN] + s[pl] : s[pl];
   }
@@ -131,48 +141,51 @@ __global__ void debug_unpack_kernel(const uint8_t* __restrict__ in, size_t n, in
 }  // namespace
 
 cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int accumulate, cudaStream_t s) {
+  const int Ns = p.vq == 4 ? p.N / 2 : p.N;
   int rows = 1;
-  while (rows * p.N < kReduceThreads && rows < p.N) rows *= 2;
+  while (rows * Ns < kReduceThreads && rows < Ns) rows *= 2;
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(p.C, p.N / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
+  dim3 grid(p.C * p.vq, Ns / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
                                         p.d_part, p.d_part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const float* part, const int* part_auto,
                              float* d_out, int accumulate, cudaStream_t s) {
+  const int Ns = p.vq == 4 ? p.N / 2 : p.N;
   int rows = 1;
-  while (rows * p.N < kReduceThreads && rows < p.N) rows *= 2;
+  while (rows * Ns < kReduceThreads && rows < Ns) rows *= 2;
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(p.C, p.N / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
+  dim3 grid(p.C * p.vq, Ns / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
                                         part, part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double2* coef64, float* d_out,
                                cudaStream_t s) {
+  const int Ns = p.vq == 4 ? p.N / 2 : p.N;
   int rows = 1;
-  while (rows * p.N < kReduceThreads && rows < p.N) rows *= 2;
+  while (rows * Ns < kReduceThreads && rows < Ns) rows *= 2;
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(p.C, p.N / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, ws.W, ws.ctas, ws.spans, p.subtract, 0, rows, p.d_part,
+  dim3 grid(p.C * p.vq, Ns / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, ws.W, ws.ctas, ws.spans, p.subtract, 0, rows, p.d_part,
                                         p.d_part_auto, coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }

@@ -91,3 +91,57 @@ def test_unsupported_shapes_are_rejected():
     w = synth.random_small(905, n_ant=8, n_pol=2, n_chan=1, grid_n=32, support=3, n_time=2)
     d, keep = epic.desc_from_workload(w, epic.XFORMS["dft_bf16x3"])
     assert epic.epic_plan_validate(d) == epic.EPIC_ERR_UNSUPPORTED
+    w = synth.random_small(906, n_ant=1025, n_pol=2, n_chan=1, grid_n=64, support=3, n_time=2)
+    d, keep = epic.desc_from_workload(w, epic.XFORMS["dft_bf16x3"])
+    assert epic.epic_plan_validate(d) == epic.EPIC_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------- 128 x 128 grids (parity split)
+@pytest.mark.parametrize("xf", ["dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+def test_grid128_random_arrays(xf):
+    """128 x 128 grids: four 64 x 64 transforms of the parity-folded fields, the
+    sub-images interleaved by the reduction."""
+    for seed, kw in [(1901, dict(n_ant=24, n_chan=3, support=5, n_time=7)),
+                     (1902, dict(n_ant=60, n_chan=2, support=3, n_time=4))]:
+        w = synth.random_small(seed, n_pol=2, grid_n=128, **kw)
+        for sub in (True, False):
+            err = rel_errors(gpu_image(w, xform=epic.XFORMS[xf], subtract=sub), oracle_image(w, subtract=sub), 2)
+            assert err.max() <= TOL[xf], (xf, seed, sub, err.max())
+
+
+def test_more_than_512_antennas():
+    """Two antennas per thread in the unpack (A up to 1024), gather entries read
+    from L2 when they do not fit in shared memory; 64^2 and 128^2."""
+    for seed, grid_n in [(1903, 64), (1904, 128)]:
+        w = synth.random_small(seed, n_ant=900, n_pol=2, n_chan=2, grid_n=grid_n, support=5, n_time=3)
+        err = rel_errors(gpu_image(w, xform=epic.XFORMS["dft_bf16x3"]), oracle_image(w), 2)
+        assert err.max() <= TOL["dft_bf16x3"], (grid_n, err.max())
+
+
+@pytest.mark.parametrize("xf", ["dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+def test_grid128_station_sampled_channels(xf):
+    """The precision study's 128^2 variant: the station block on a 2x padded
+    grid, full size, channels 0, 40, 63 against the oracle's FFT mode."""
+    w = _station128()
+    got = gpu_image(w, xform=epic.XFORMS[xf])
+    chans = [0, 40, 63]
+    ref = _station128_ref(chans)
+    err = rel_errors(got[chans], ref, 2)
+    print(f"128^2 {xf}: max error / image peak per plane {err.max(axis=0)}")
+    assert err.max() <= TOL[xf]
+
+
+_S128 = {}
+
+
+def _station128():
+    if "w" not in _S128:
+        _S128["w"] = synth.station(grid_n=128)
+    return _S128["w"]
+
+
+def _station128_ref(chans):
+    key = tuple(chans)
+    if key not in _S128:
+        _S128[key] = oracle_image(_station128(), channels=chans, use_fft=True)
+    return _S128[key]
