@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--soak-seconds", type=float, default=1.5)
     ap.add_argument("--grid128-steps", type=int, default=20,
                     help="calls timed on the station block at 128 x 128 (0 to skip)")
+    ap.add_argument("--grid128-paths", default="fft_fp32,dft_bf16x3,dft_fp16",
+                    help="transforms timed on the station block at 128 x 128")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="graph launches timed for the batching workload (0 to skip)")
     ap.add_argument("--grad-steps", type=int, default=20,
@@ -236,61 +238,67 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------
 def time_grid128(args, epic, synth, torch, stream, world, shard, sms, pk, pk_kind):
-    """The station block imaged on a 2x padded 128 x 128 grid (FP32 path, clusters
-    of two CTAs), with its kernel's fraction of the FP32 peak."""
+    """The station block imaged on a 2x padded 128 x 128 grid (the precision
+    study's 128^2 variant): the FP32 path (clusters of two CTAs) and the tensor
+    paths (four 64 x 64 DFT-GEMMs per image set), each with its kernel's
+    fraction of its roofline."""
     w = synth.station(grid_n=128)
-    plan = epic.plan_for(w)
     dv = [torch.from_numpy(w.volts).cuda() for _ in range(2)]
-    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
-    for i in range(3):
-        epic.epic_image(plan, dv[i % 2], w.n_time, out, 0, stream)
-    torch.cuda.synchronize()
-    epic.epic_timing_enable(plan, True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.grid128_steps):
-        epic.epic_image(plan, dv[i % 2], w.n_time, out, 0, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.grid128_steps, device="cuda")
-    kt = epic.epic_timing_read(plan)
-    epic.epic_timing_enable(plan, False)
-    epic.epic_sync(plan)
-    n, tot = kt["fft_image"]
-    avg_s = tot / n / 1e3
-    flops = w.n_chan * w.n_time * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
-    peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     res = {"workload": "station block (256 dual-pol antennas, 64 channels, 1250 samples, 5x5) on a 2x padded "
-                       "128x128 grid", "xform": "fft_fp32", "error_bound": ERROR_BOUND["fft_fp32"],
-           "ms_per_call": ms, "value": w.units * world / (ms / 1e3), "unit": UNIT,
-           "roofline": {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "frac": flops / avg_s / 1e12 / peak, "kernel": "fft_image (N = 128, 2-CTA clusters)",
-                        "kernel_ms": 1e3 * avg_s, "flops_per_launch": flops,
-                        "traffic": dram_traffic("fft128_image", "epic_fft128.cu"),
-                        "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
-                                      f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind})"},
-           "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kt.items()},
-           "clusters": plan.info["ctas"]}
-    plan.close()
+                       "128x128 grid"}
+    for xf in [x for x in args.grid128_paths.split(",") if x]:
+        plan = epic.plan_for(w, epic.XFORMS[xf])
+        out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+        for i in range(3):
+            epic.epic_image(plan, dv[i % 2], w.n_time, out, 0, stream)
+        torch.cuda.synchronize()
+        epic.epic_timing_enable(plan, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.grid128_steps):
+            epic.epic_image(plan, dv[i % 2], w.n_time, out, 0, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.grid128_steps, device="cuda")
+        kt = epic.epic_timing_read(plan)
+        epic.epic_timing_enable(plan, False)
+        epic.epic_sync(plan)
+        kname = "fft_image" if xf == "fft_fp32" else "dft_image"
+        n, tot = kt[kname]
+        avg_s = tot / n / 1e3
+        if xf == "fft_fp32":
+            flops = w.n_chan * w.n_time * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
+            peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": "fft128_image (2-CTA clusters)",
+                    "traffic": dram_traffic("fft128_image", "epic_fft128.cu"),
+                    "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
+                                  f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind})"}
+        else:
+            flops = w.n_chan * w.n_time * 4 * tensor_flops_per_tc(xf)
+            peak = pk.get("bf16_tflops", 1900.0)
+            roof = {"bound": "tensor", "kernel": "dft_image (4 parity sub-problems of 64x64 per image set)",
+                    "traffic": dram_traffic("dft_image_128", "epic_dft.cu") if xf == "dft_bf16x3" else None,
+                    "peak_basis": f"measured dense BF16 cuBLAS burst ({pk_kind})",
+                    "useful_tflops": flops / (3 if xf.endswith("x3") else 1) / avg_s / 1e12}
+        roof.update({"achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / avg_s / 1e12 / peak, "kernel_ms": 1e3 * avg_s, "flops_per_launch": flops})
+        res[xf] = {"ms_per_call": ms, "value": w.units * world / (ms / 1e3), "unit": UNIT,
+                   "error_bound": ERROR_BOUND[xf], "roofline": roof,
+                   "kernel_times_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kt.items()}}
+        plan.close()
     return res
 
 
-def time_batch(args, epic, synth, torch, stream, world, shard):
-    """Arrays A, B and C of the batching recipe (T = 1250 each), every plan that
-    the library supports in one autotuned graph; also the same plans imaged by
-    separate epic_image calls one after another, for comparison."""
-    ws, plans, skipped = [], [], {}
-    for k in ("A", "B", "C"):
-        w = synth.batching_array(k)
-        try:
-            plans.append(epic.plan_for(w))
-            ws.append(w)
-        except epic.EpicError as e:
-            skipped[k] = epic.epic_status_string(e.status)
+def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
+    """Arrays A, B and C of the batching recipe (T = 1250 each) in one autotuned
+    graph launch, twice: every array on the FP32 path, and the tensor-core batch
+    (arrays B and C on the compensated BF16 path, array A -- a 32 x 32 grid,
+    which the tensor path does not take -- on the FP32 path).  The same plans
+    imaged by separate epic_image calls one after another are timed for
+    comparison."""
+    ws = [synth.batching_array(k) for k in ("A", "B", "C")]
     vols = [torch.from_numpy(w.volts).cuda() for w in ws]
-    outs = [torch.empty(p.out_shape, dtype=torch.float32, device="cuda") for p in plans]
-    b = epic.epic_batch_create(plans, vols, [w.n_time for w in ws], outs, tune=True, stream=stream)
 
     def timed(fn, n):
         for _ in range(3):
@@ -305,22 +313,38 @@ def time_batch(args, epic, synth, torch, stream, world, shard):
         torch.cuda.synchronize()
         return shard.max_over_ranks(e0.elapsed_time(e1) / n, device="cuda")
 
-    ms = timed(lambda: epic.epic_batch_launch(b, stream), args.batch_steps)
+    res = {}
+    for name, xforms in (("fp32", ["fft_fp32"] * 3), ("tensor", ["fft_fp32", "dft_bf16x3", "dft_bf16x3"])):
+        plans = [epic.plan_for(w, epic.XFORMS[x]) for w, x in zip(ws, xforms)]
+        outs = [torch.empty(p.out_shape, dtype=torch.float32, device="cuda") for p in plans]
+        b = epic.epic_batch_create(plans, vols, [w.n_time for w in ws], outs, tune=True, stream=stream)
+        ms = timed(lambda: epic.epic_batch_launch(b, stream), args.batch_steps)
 
-    def separate():
-        for p, v, w, o in zip(plans, vols, ws, outs):
-            epic.epic_image(p, v, w.n_time, o, 0, stream)
+        def separate():
+            for p, v, w, o in zip(plans, vols, ws, outs):
+                epic.epic_image(p, v, w.n_time, o, 0, stream)
 
-    ms_sep = timed(separate, args.batch_steps)
-    units = sum(w.units for w in ws)
-    res = {"workload": "batching arrays " + "+".join(w.name[-1] for w in ws) + ", T = 1250 each, one graph launch",
-           "ms_per_launch": ms, "value": units * world / (ms / 1e3), "unit": UNIT,
-           "units_per_launch": units, "ctas_chosen": dict(zip([w.name for w in ws], b.ctas)),
-           "ms_separate_calls": ms_sep, "graph_launches_per_step": 1,
-           "kernel_launches_per_step": 2 * len(plans), "not_in_batch": skipped}
-    b.close()
-    for p in plans:
-        p.close()
+        ms_sep = timed(separate, args.batch_steps)
+        units = sum(w.units for w in ws)
+        r = {"ms_per_launch": ms, "value": units * world / (ms / 1e3), "unit": UNIT, "units_per_launch": units,
+             "xforms": dict(zip([w.name for w in ws], xforms)), "ctas_chosen": dict(zip([w.name for w in ws], b.ctas)),
+             "ms_separate_calls": ms_sep, "graph_launches_per_step": 1, "kernel_launches_per_step": 2 * len(plans)}
+        if name == "tensor":
+            # issued tensor-core flops of the batch over the graph time (the FP32
+            # array A is 2 % of the units and counted at zero)
+            fl = sum(w.n_chan * w.n_time * (4 if w.grid_n == 128 else 1) * tensor_flops_per_tc(x)
+                     for w, x in zip(ws, xforms) if x != "fft_fp32")
+            peak = pk.get("bf16_tflops", 1900.0)
+            r["roofline"] = {"bound": "tensor", "achieved": fl / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": fl / (ms / 1e3) / 1e12 / peak, "flops_per_launch": fl,
+                             "basis": f"issued BF16 x3 flops of arrays B and C over the whole graph time; "
+                                      f"peak: measured dense BF16 cuBLAS burst ({pk_kind})"}
+        res[name] = r
+        b.close()
+        for p in plans:
+            p.close()
+    res["workload"] = "batching arrays A (64 ants, 32x32, 16 ch) + B (station, 64x64, 64 ch) + C (1024 ants, " \
+                      "220 m, 128x128, 32 ch), T = 1250 each, one graph launch"
     return res
 
 
@@ -493,7 +517,7 @@ def main():
     # batching: the arrays of the batching recipe imaged by one graph launch
     batch = None
     if args.batch_steps > 0:
-        batch = time_batch(args, epic, synth, torch, stream, world, shard)
+        batch = time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
