@@ -114,7 +114,7 @@ def test_coefficient_closed_form(oracle_lib):
 # --------------------------------------------------------------------------
 # Step 5: the transform (Eq. (5) sign, reading R3/R4) against numpy
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("N", [4, 8, 16, 32, 64])
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 64, 128])
 def test_dft2_is_shifted_unnormalised_inverse_fft(oracle_lib, N):
     rng = np.random.default_rng(N)
     g = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
@@ -142,6 +142,8 @@ CASES = [
     dict(seed=3, n_ant=4, n_pol=2, n_chan=1, grid_n=16, support=5),
     dict(seed=4, n_ant=7, n_pol=2, n_chan=2, grid_n=8, support=3, with_gains=False, with_delays=False),
     dict(seed=5, n_ant=3, n_pol=1, n_chan=3, grid_n=16, support=5, n_time=9),
+    # the grid size of the 128^2 variants (2x padded station, batching array C)
+    dict(seed=6, n_ant=6, n_pol=2, n_chan=1, grid_n=128, support=5, n_time=3),
 ]
 
 
