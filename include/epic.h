@@ -108,9 +108,10 @@ typedef struct {
  * in some channel) or EPIC_ERR_UNSUPPORTED (a grid size or transform this
  * build does not implement: the FP32 FFT path takes N = 32 or 64 with at most
  * 2048 antennas, or N = 128 with at most 1024 antennas (imaged by clusters of
- * two CTAs); the tensor-core paths take N = 64 or 128 (a 128 x 128 grid is
- * transformed as four 64 x 64 parity sub-problems), two polarisations and at
- * most 1024 antennas). */
+ * two CTAs); the tensor-core paths take N = 32, 64 or 128 (a 128 x 128 grid
+ * is transformed as four 64 x 64 parity sub-problems, a 32 x 32 grid as one
+ * zero-padded 64 x 64 problem), two polarisations and at most 1024
+ * antennas). */
 epic_status epic_plan_validate(const epic_plan_desc* desc);
 
 /* Creates a plan on the current CUDA device: validates desc, copies its

@@ -34,7 +34,7 @@ bool grid_supported(int xform, int N, int P, int A, int S) {
   // tensor path: 64 x 64 or 128 x 128 grids of two polarisations, up to 1024
   // antennas (gather entries in shared memory when they fit, else read from L2)
   (void)S;
-  return (N == 64 || N == 128) && P == 2 && A <= 1024 && epic::dft_smem_need(A, 0) <= kSmemOptin;
+  return (N == 32 || N == 64 || N == 128) && P == 2 && A <= 1024 && epic::dft_smem_need(A, 0) <= kSmemOptin;
 }
 
 epic_status from_cuda(cudaError_t e) {
@@ -308,9 +308,12 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
     total += gt_bytes;
     EPIC_TRY(epic::fft_image_config(p, &per_sm));
   } else {
-    // N = 128: four virtual channels per channel, one per output-parity subset
+    // N = 128: four virtual channels per channel, one per output-parity subset;
+    // N = 32: the 64 x 64 transform of the zero-padded grid, even pixels kept
     p.vq = p.N == 128 ? 4 : 1;
-    EPIC_TRY(epic::build_gather_tables(p, p.N == 128 ? epic::kLayoutPairQ : epic::kLayoutPair64, 512, 0, &gt_bytes));
+    p.dec = p.N == 32 ? 2 : 1;
+    const int layout = p.N == 128 ? epic::kLayoutPairQ : p.N == 32 ? epic::kLayoutPairD : epic::kLayoutPair64;
+    EPIC_TRY(epic::build_gather_tables(p, layout, 512, 0, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(alloc(&p.d_fmat, (size_t)4 * 128 * 128 / 2, &total));
     EPIC_TRY(epic::launch_dft_tables(p, 0));
@@ -321,7 +324,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   p.ctas = clusters > 0 ? clusters : p.sm_count * per_sm;
   p.spans = (p.C * p.vq + p.ctas - 1) / p.ctas + 2;
   size_t before = total;
-  const size_t Ns = p.vq == 4 ? N / 2 : N;  // side of a partial image
+  const size_t Ns = p.vq == 4 ? N / 2 : N * p.dec;  // side of a partial image
   EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * Ns * Ns, &total));
   EPIC_TRY(alloc(&p.d_part_auto, (size_t)p.ctas * p.spans * A * 4, &total));
   p.workspace_bytes = total - before;

@@ -27,6 +27,9 @@
 //           (-1)^(alpha s + beta u) (alpha = q & 1, beta = q >> 1); its entry
 //           list is the four cells' lists in (u, s) order, weights signed.  One
 //           table set per virtual channel 4 c + q.
+//   kPairD: the same over a 64 x 64 field holding a 32 x 32 grid in its cells
+//           y, x < 32 (zero elsewhere): the tensor path's transform of 32 x 32
+//           grids, whose even output pixels are the 32-point transform.
 // With sorting on, tasks are ordered by their number of entries (stable), so
 // warps get cells of similar load; thread i of a channel then works on task
 // task[i].
@@ -45,10 +48,20 @@ __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
   }
 }
 
+// Grid cell of field cell (y, x), or -1 where the field is zero (kLayoutPairD
+// outside the 32 x 32 grid); not used by kLayoutPairQ.
+__device__ __forceinline__ int field_cell(int layout, int N, int y, int x) {
+  if (layout == kLayoutPairD) return (y < N && x < N) ? y * N + x : -1;
+  return y * N + x;
+}
+
 // Entries of cell (y, x) of the gathered field: a grid cell, or for kLayoutPairQ
 // the four grid cells folded into H_q(y, x).
 __device__ __forceinline__ int field_count(int layout, const int* ptr, int N, int y, int x) {
-  if (layout != kLayoutPairQ) return ptr[y * N + x + 1] - ptr[y * N + x];
+  if (layout != kLayoutPairQ) {
+    const int cell = field_cell(layout, N, y, x);
+    return cell < 0 ? 0 : ptr[cell + 1] - ptr[cell];
+  }
   int n = 0;
   for (int us = 0; us < 4; ++us) {
     const int cell = (y + 64 * (us >> 1)) * N + x + 64 * (us & 1);
@@ -92,7 +105,7 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   const int ns = layout == kLayoutFft128 ? 16 : 8;  // slots per thread
   int* kws = sh;                 // [warps * ns]
   int* bws = kws + warps * ns;   // [warps * ns]
-  const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ;
+  const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
   int* keys = bws + warps * ns;  // [nt], or [2048] for pairs
   int* perm = keys + (pairs ? 2048 : nt);     // [nt], or [2048]
   int* pair_of = perm + (pairs ? 2048 : nt);  // [4 nt] (pairs only)
@@ -130,7 +143,8 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   int cnt[16], beg[16];
   for (int s = 0; s < ns; ++s) {
     const int2 yx = cells[s];
-    beg[s] = layout == kLayoutPairQ ? 0 : ptr[yx.x * N + yx.y];
+    const int cell = layout == kLayoutPairQ ? -1 : field_cell(layout, N, yx.x, yx.y);
+    beg[s] = cell < 0 ? 0 : ptr[cell];
     cnt[s] = field_count(layout, ptr, N, yx.x, yx.y);
     // FFT layouts: trip count rounded up to even (that kernel walks entries in pairs)
     const int kmax = __reduce_max_sync(0xffffffffu, cnt[s]);
@@ -208,7 +222,7 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   const int warps = threads / 32;
   const int ns = layout == kLayoutFft128 ? 16 : 8;
   const int nnz = p.A * p.S * p.S;
-  const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ;
+  const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
   const int nsets = layout == kLayoutPairQ ? 4 * p.C : p.C;  // table sets (virtual channels)
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
                                      (pairs ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));

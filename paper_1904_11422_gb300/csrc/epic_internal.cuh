@@ -40,7 +40,7 @@ struct WorkSplit {
 
 // Gather tables of a gridder (see epic_gather.cu).
 enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3, kLayoutFft128 = 4,
-             kLayoutPairQ = 5 };
+             kLayoutPairQ = 5, kLayoutPairD = 6 };
 struct GatherTables {
   int layout = 0, threads = 0, sorted = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel
@@ -56,6 +56,7 @@ struct Plan {
   // descriptor copy
   int A, P, C, N, S, xform, subtract;
   int vq = 1;  // virtual channels per channel: 4 for the tensor path at N = 128 (output-parity subsets)
+  int dec = 1; // 2 for the tensor path at N = 32: a 64 x 64 transform of the zero-padded grid, even pixels kept
   double cell_lambda, sigma;
   int device, sm_count;
 

@@ -17,10 +17,13 @@ constexpr int kReduceThreads = 256;
 // One block per (channel, `rows` rows).  With vq = 4 (the tensor path on
 // 128 x 128 grids) the partials are the 64 x 64 sub-images of virtual channels
 // 4 c + q, and pixel (j, i) of sub-image q lands on output pixel
-// (2 j + beta, 2 i + alpha), alpha = q & 1, beta = q >> 1.
+// (2 j + beta, 2 i + alpha), alpha = q & 1, beta = q >> 1.  With dec = 2 (the
+// tensor path on 32 x 32 grids) the partials are 64 x 64 and output pixel (j, i)
+// is their pixel (2 j, 2 i).
 template <int P>
 __global__ void __launch_bounds__(kReduceThreads)
-    reduce_kernel(int T, int C, int A, int N, int vq, long long W, int ctas, int spans, int subtract, int accumulate,
+    reduce_kernel(int T, int C, int A, int N, int vq, int dec, long long W, int ctas, int spans, int subtract,
+                  int accumulate,
                   int rows, const float* __restrict__ part, const int* __restrict__ part_auto,
                   const double2* __restrict__ coef64, const float* __restrict__ kx2, const float* __restrict__ ky2,
                   float* __restrict__ out) {
@@ -30,7 +33,8 @@ __global__ void __launch_bounds__(kReduceThreads)
   const int cv = blockIdx.x;                           // (virtual) channel of the partials
   const int c = vq == 4 ? cv >> 2 : cv;                // output channel
   const int alpha = vq == 4 ? (cv & 1) : 0, beta = vq == 4 ? (cv >> 1) & 1 : 0;
-  const int Ns = vq == 4 ? N / 2 : N;                  // side of a partial image
+  const int Ns = vq == 4 ? N / 2 : N * dec;            // side of a partial image
+  const int L = vq == 4 ? Ns : N;                      // side of the pixel loop
   const int j0 = blockIdx.y * rows;
   const int NN = N * N, NNs = Ns * Ns;
   auto orow = [&](int j) { return vq == 4 ? 2 * j + beta : j; };
@@ -61,8 +65,8 @@ __global__ void __launch_bounds__(kReduceThreads)
     __syncthreads();
   }
 
-  for (int q = threadIdx.x; q < rows * Ns; q += blockDim.x) {
-    const int jj = q / Ns, i = q % Ns, pix = (j0 + jj) * Ns + i;
+  for (int q = threadIdx.x; q < rows * L; q += blockDim.x) {
+    const int jj = q / L, i = q % L, pix = dec * (j0 + jj) * Ns + dec * i;
     const int opix = orow(j0 + jj) * N + ocol(i);
     float s[4] = {0.f, 0.f, 0.f, 0.f};
     for (long long b = b_lo; b <= b_hi; ++b) {
@@ -141,51 +145,51 @@ __global__ void debug_unpack_kernel(const uint8_t* __restrict__ in, size_t n, in
 }  // namespace
 
 cudaError_t launch_reduce(Plan& p, int T, const WorkSplit& ws, float* d_out, int accumulate, cudaStream_t s) {
-  const int Ns = p.vq == 4 ? p.N / 2 : p.N;
+  const int L = p.vq == 4 ? p.N / 2 : p.N;  // side of the reduction's pixel loop
   int rows = 1;
-  while (rows * Ns < kReduceThreads && rows < Ns) rows *= 2;
+  while (rows * L < kReduceThreads && rows < L) rows *= 2;
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(p.C * p.vq, Ns / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
+  dim3 grid(p.C * p.vq, L / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, p.dec, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
                                         p.d_part, p.d_part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const float* part, const int* part_auto,
                              float* d_out, int accumulate, cudaStream_t s) {
-  const int Ns = p.vq == 4 ? p.N / 2 : p.N;
+  const int L = p.vq == 4 ? p.N / 2 : p.N;  // side of the reduction's pixel loop
   int rows = 1;
-  while (rows * Ns < kReduceThreads && rows < Ns) rows *= 2;
+  while (rows * L < kReduceThreads && rows < L) rows *= 2;
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(p.C * p.vq, Ns / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
+  dim3 grid(p.C * p.vq, L / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, p.dec, ws.W, ws.ctas, ws.spans, p.subtract, accumulate, rows,
                                         part, part_auto, p.d_coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_coef(Plan& p, int T, const WorkSplit& ws, const double2* coef64, float* d_out,
                                cudaStream_t s) {
-  const int Ns = p.vq == 4 ? p.N / 2 : p.N;
+  const int L = p.vq == 4 ? p.N / 2 : p.N;  // side of the reduction's pixel loop
   int rows = 1;
-  while (rows * Ns < kReduceThreads && rows < Ns) rows *= 2;
+  while (rows * L < kReduceThreads && rows < L) rows *= 2;
   const size_t smem = p.subtract ? (sizeof(float4) * p.A + sizeof(float) * (size_t)p.A * rows) : 16;
   auto fn = p.P == 2 ? reduce_kernel<2> : reduce_kernel<1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(fn);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(p.C * p.vq, Ns / rows);
-  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, ws.W, ws.ctas, ws.spans, p.subtract, 0, rows, p.d_part,
+  dim3 grid(p.C * p.vq, L / rows);
+  fn<<<grid, kReduceThreads, smem, s>>>(T, p.C, p.A, p.N, p.vq, p.dec, ws.W, ws.ctas, ws.spans, p.subtract, 0, rows, p.d_part,
                                         p.d_part_auto, coef64, p.d_kx2, p.d_ky2, d_out);
   return cudaGetLastError();
 }

@@ -88,7 +88,7 @@ def test_validate_accepts_valid(lib):
     (dict(n_pol=3, gains=None, delays_s=None), epic.EPIC_ERR_INVALID_ARG),
     (dict(grid_n=48), epic.EPIC_ERR_INVALID_ARG),
     (dict(grid_n=256), epic.EPIC_ERR_UNSUPPORTED),
-    (dict(grid_n=32, xform=1), epic.EPIC_ERR_UNSUPPORTED),
+    (dict(n_pol=1, xform=1, gains=None, delays_s=None), epic.EPIC_ERR_UNSUPPORTED),
     (dict(cell_lambda=0.0), epic.EPIC_ERR_INVALID_ARG),
     (dict(kernel_sigma_cells=-1.0), epic.EPIC_ERR_INVALID_ARG),
     (dict(chan_freq_hz=[50e6, -1.0]), epic.EPIC_ERR_INVALID_ARG),

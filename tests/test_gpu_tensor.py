@@ -88,7 +88,7 @@ def test_unsupported_shapes_are_rejected():
     w = synth.random_small(904, n_ant=8, n_pol=1, n_chan=1, grid_n=64, support=3, n_time=2)
     d, keep = epic.desc_from_workload(w, epic.XFORMS["dft_bf16x3"])
     assert epic.epic_plan_validate(d) == epic.EPIC_ERR_UNSUPPORTED
-    w = synth.random_small(905, n_ant=8, n_pol=2, n_chan=1, grid_n=32, support=3, n_time=2)
+    w = synth.random_small(905, n_ant=8, n_pol=2, n_chan=1, grid_n=16, support=3, n_time=2)
     d, keep = epic.desc_from_workload(w, epic.XFORMS["dft_bf16x3"])
     assert epic.epic_plan_validate(d) == epic.EPIC_ERR_UNSUPPORTED
     w = synth.random_small(906, n_ant=1025, n_pol=2, n_chan=1, grid_n=64, support=3, n_time=2)
@@ -145,3 +145,16 @@ def _station128_ref(chans):
     if key not in _S128:
         _S128[key] = oracle_image(_station128(), channels=chans, use_fft=True)
     return _S128[key]
+
+
+# ---------------------------------------------- 32 x 32 grids (zero-padded to 64)
+@pytest.mark.parametrize("xf", ["dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+def test_grid32_random_arrays(xf):
+    """32 x 32 grids: the 64 x 64 transform of the zero-padded grid, whose even
+    output pixels are the 32-point transform."""
+    for seed, kw in [(2001, dict(n_ant=16, n_chan=3, support=3, n_time=9)),
+                     (2002, dict(n_ant=40, n_chan=2, support=5, n_time=5))]:
+        w = synth.random_small(seed, n_pol=2, grid_n=32, **kw)
+        for sub in (True, False):
+            err = rel_errors(gpu_image(w, xform=epic.XFORMS[xf], subtract=sub), oracle_image(w, subtract=sub), 2)
+            assert err.max() <= TOL[xf], (xf, seed, sub, err.max())
