@@ -64,7 +64,7 @@ void free_plan(Plan& p) {
   void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
                   p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
                   p.d_stage_in, p.d_stage_out, p.d_fmat, p.d_dphase, p.d_gcoef, p.d_gcoef64, p.d_gimage,
-                  p.d_resid, p.d_loss_part, p.d_gpart, p.d_beam};
+                  p.d_resid, p.d_loss_part, p.d_gpart, p.d_beam, p.d_xbuf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   epic::free_gather_tables(p.gt);
@@ -327,6 +327,8 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   const size_t Ns = p.vq == 4 ? N / 2 : N * p.dec;  // side of a partial image
   EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * Ns * Ns, &total));
   EPIC_TRY(alloc(&p.d_part_auto, (size_t)p.ctas * p.spans * A * 4, &total));
+  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128)
+    EPIC_TRY(alloc(&p.d_xbuf, epic::fft128_xbuf_elems(p.ctas, p.P), &total));
   p.workspace_bytes = total - before;
   // epic_grad: FP32 FFT plans of 64 x 64 grids with one antenna per thread
   if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 64 && p.A <= 512 && epic::adjoint_smem_need(p) <= kSmemOptin) {

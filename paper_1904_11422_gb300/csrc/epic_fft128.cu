@@ -7,15 +7,21 @@
 // are another 256 KB.  The pair splits both:
 //   * CTA r grids and row-transforms the rows y in [64 r, 64 r + 64) of both
 //     polarisations, in its own shared memory (128 KB);
-//   * after a cluster barrier, CTA r column-transforms the columns k in
-//     [64 r, 64 r + 64), reading the half of each column held by the other CTA
-//     through distributed shared memory;
+//   * the row outputs in the other CTA's columns go to a small exchange buffer
+//     in global memory (L2) instead of the own row buffer; after a cluster
+//     barrier (release / acquire at cluster scope), CTA r column-transforms the
+//     columns k in [64 r, 64 r + 64), reading its own rows from shared memory
+//     and the other CTA's rows from the exchange buffer;
 //   * the squared and cross-multiplied outputs of its columns are accumulated
 //     in tensor memory (TMEM, 128 KB per CTA: 512 threads x 64 FP32 values),
 //     which stays resident for the cluster's whole span of samples.
-// A second cluster barrier, after the column loads, lets each CTA reuse its row
-// buffer as exchange scratch for its column transforms.  Both CTAs of a cluster
-// walk the same units, so they reach every barrier the same number of times.
+// The exchange buffer is double-buffered by sample parity: a CTA writes sample
+// u + 2 only after the barrier of sample u + 1, which the other CTA reaches after
+// reading sample u.  Fine-grained distributed shared memory was measured to move
+// only about 11 bytes per clock per SM for this pattern (loads or stores), a
+// quarter of the kernel's time; through L2 the same 64 KB per sample and CTA
+// costs far less.  Both CTAs of a cluster walk the same units, so they reach
+// every barrier the same number of times.
 //
 // Line transforms: 128 = 16 x 8 (Cooley-Tukey).  A line is held by 8 threads,
 // thread n1 holding elements n1 + 8 n2 (n2 = 0..15); it takes the 16-point DFT
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int* __restrict__ g_base, const int* __restrict__ g_off,
                         const uint16_t* __restrict__ g_ent_a, const float* __restrict__ g_ent_w, int max_entries,
                         int ent_in_smem, const float2* __restrict__ twiddle, float* __restrict__ part,
-                        int* __restrict__ part_auto) {
+                        int* __restrict__ part_auto, float2* __restrict__ xbuf) {
   constexpr int NN = kN * kN, HALF = kN / 2;
   constexpr int NPL = (P == 2) ? 4 : 1;
 
@@ -195,11 +201,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   // lane quarter of this warp, and its 64 accumulator columns (4 planes x 16)
   const uint32_t tacc = *taddr_s + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
-  // both CTAs are running before either reads the other's shared memory
-  cluster_sync();
-
-  const uint32_t R_local = smem_u32(Rbuf);
-  const uint32_t R_peer = map_shared(R_local, rank ^ 1u);
+  // exchange buffers of this cluster: [parity][writer rank][P][64 columns][8 j][8 m1]
+  // holding the writer's row y = 64 rank + m1 + 8 j in the reader's column 64 (1 - rank) + k
+  constexpr size_t kXSlab = (size_t)P * kRows * kRows;  // float2 per (parity, writer)
+  float2* xb = xbuf + (size_t)cluster * 4 * kXSlab;
 
   unsigned raw[kMaxK] = {}, raw_next[kMaxK] = {};
   auto load_raw = [&](long long u, unsigned (&dst)[kMaxK]) {
@@ -246,7 +251,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
 
+  // 1. unpack, calibrate, exact integer self powers (kept by CTA 0)
+  auto unpack = [&](const unsigned (&rw)[kMaxK]) {
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+      const int a = tid + k * kThreads;
+      if (a < A) {
+        const int xr = nib_hi(rw[k] & 0xffu), xi = nib_lo(rw[k] & 0xffu);
+        const float2 kx = coef_s[a * P];
+        const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
+        int4 au = auto_s[a];
+        au.x += xr * xr + xi * xi;
+        if constexpr (P == 2) {
+          const int yr = nib_hi(rw[k] >> 8), yi = nib_lo(rw[k] >> 8);
+          const float2 ky = coef_s[a * P + 1];
+          const float2 ey = make_float2(ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
+          E4[a] = make_float4(ex.x, ex.y, ey.x, ey.y);
+          au.y += yr * yr + yi * yi;
+          au.z += xr * yr + xi * yi;
+          au.w += xi * yr - xr * yi;
+        } else {
+          E2[a] = ex;
+        }
+        if (rank == 0) auto_s[a] = au;
+      }
+    }
+  };
+
   int cur_c = -1, eoff = 0;
+  bool have_next = false;
   const uint16_t* ent_a = g_ent_a;
   const float* ent_w = g_ent_w;
 
@@ -286,31 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (u + 1 < u1) load_raw(u + 1, raw_next);
 
-    // 1. unpack, calibrate, exact integer self powers (kept by CTA 0)
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-      const int a = tid + k * kThreads;
-      if (a < A) {
-        const int xr = nib_hi(raw[k] & 0xffu), xi = nib_lo(raw[k] & 0xffu);
-        const float2 kx = coef_s[a * P];
-        const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
-        int4 au = auto_s[a];
-        au.x += xr * xr + xi * xi;
-        if constexpr (P == 2) {
-          const int yr = nib_hi(raw[k] >> 8), yi = nib_lo(raw[k] >> 8);
-          const float2 ky = coef_s[a * P + 1];
-          const float2 ey = make_float2(ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
-          E4[a] = make_float4(ex.x, ex.y, ey.x, ey.y);
-          au.y += yr * yr + yi * yi;
-          au.z += xr * yr + xi * yi;
-          au.w += xi * yr - xr * yi;
-        } else {
-          E2[a] = ex;
-        }
-        if (rank == 0) auto_s[a] = au;
-      }
+    // E holds this sample's fields already when they were unpacked while the
+    // previous sample waited at its cluster barrier
+    if (!have_next) {
+      unpack(raw);
+      __syncthreads();
     }
-    __syncthreads();
+    have_next = false;
 
     // 2. grid (gather, fixed order) and 3a. row transforms; thread (local row
     //    `line`, n1) owns cells (64 rank + line, n1 + 8 n2).  A warp whose four
@@ -344,33 +359,51 @@ __global__ void __launch_bounds__(kThreads, 1)
         v[0][n2] = gx;
         if constexpr (P == 2) v[1][n2] = gy;
       }
+      // this sample's exchange slab written by this CTA
+      float2* xw = xb + (size_t)(((u - u0) & 1) * 2 + rank) * kXSlab;
+      const int m1w = line & 7, jw = line >> 3;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         float2* row = Rbuf + (size_t)(p * kRows + line) * kN;
         if (any) fft_line128(v[p], tw_s, row, line, n1);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) row[cpos(line, kidx(n1, s))] = v[p][s];
+        for (int s = 0; s < 16; ++s) {
+          const int k = kidx(n1, s);
+          if ((k >> 6) == (int)rank)
+            row[cpos(line, k)] = v[p][s];
+          else
+            __stcg(xw + (((size_t)p * kRows + (k & 63)) * 8 + jw) * 8 + m1w, v[p][s]);
+        }
       }
     }
-    // rows of both CTAs complete
-    cluster_sync();
+    // rows of both CTAs complete, in shared memory and in the exchange buffer;
+    // while the release of the exchange writes completes, unpack the next
+    // sample of the same channel (every thread has finished reading E)
+    __syncthreads();
+    cluster_arrive();
+    if (u + 1 < u1 && (int)((u + 1) / T) == c) {
+      unpack(raw_next);
+      have_next = true;
+    }
+    cluster_wait();
 
     // 3b. column transforms and 4. products; thread (column 64 rank + line, m1 = n1)
     {
       float2 v[P][16];
+      // row n1 + 8 m2 is local row n1 + 8 (m2 & 7) of CTA m2 / 8
+      const float2* xr = xb + (size_t)(((u - u0) & 1) * 2 + (rank ^ 1u)) * kXSlab;
 #pragma unroll
       for (int p = 0; p < P; ++p)
 #pragma unroll
         for (int m2 = 0; m2 < 16; ++m2) {
-          const int yl = n1 + 8 * (m2 & 7);  // row n1 + 8 m2 is local row yl of CTA m2 / 8
-          const int idx = (p * kRows + yl) * kN + cpos(yl, kglob);
+          const int j = m2 & 7, yl = n1 + 8 * j;
           if ((m2 >> 3) == (int)rank)
-            v[p][m2] = Rbuf[idx];
+            v[p][m2] = Rbuf[(p * kRows + yl) * kN + cpos(yl, kglob)];
           else
-            v[p][m2] = ld_cluster_f2(R_peer + 8u * (uint32_t)idx);
+            v[p][m2] = __ldcg(xr + (((size_t)p * kRows + line) * 8 + j) * 8 + n1);
         }
-      // both CTAs have read what they need; the row buffers become scratch
-      cluster_sync();
+      // every thread of this CTA has read its rows; the row buffers become scratch
+      __syncthreads();
 #pragma unroll
       for (int p = 0; p < P; ++p) fft_line128(v[p], tw_s, Rbuf + (size_t)(p * kRows + line) * kN, line, n1);
 
@@ -455,7 +488,7 @@ cudaError_t config(Plan& p, int* clusters) {
 
 template <int P>
 cudaError_t launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part, int* part_auto,
-                   cudaStream_t s) {
+                   float2* xbuf, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -471,7 +504,8 @@ cudaError_t launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit
   return cudaLaunchKernelEx(&cfg, fft128_image_kernel<P>, d_volts, T, p.C, p.A, (long long)ws.W, ws.units,
                             ws.spans, (const float2*)p.d_coef, (const int*)p.gt.d_cnt, (const int*)p.gt.d_base,
                             (const int*)p.gt.d_chan_off, (const uint16_t*)p.gt.d_ent_a, (const float*)p.gt.d_ent_w,
-                            p.gt.max_chan_entries, p.ent_in_smem, (const float2*)p.d_twiddle, part, part_auto);
+                            p.gt.max_chan_entries, p.ent_in_smem, (const float2*)p.d_twiddle, part, part_auto,
+                            xbuf);
 }
 
 }  // namespace
@@ -485,9 +519,12 @@ cudaError_t fft128_config(Plan& p, int* clusters) {
   return p.P == 2 ? config<2>(p, clusters) : config<1>(p, clusters);
 }
 
+size_t fft128_xbuf_elems(int clusters, int P) { return (size_t)clusters * 4 * P * kRows * kRows; }
+
 cudaError_t launch_fft128_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                                    int* part_auto, cudaStream_t s) {
-  return p.P == 2 ? launch<2>(p, d_volts, T, ws, part, part_auto, s) : launch<1>(p, d_volts, T, ws, part, part_auto, s);
+  return p.P == 2 ? launch<2>(p, d_volts, T, ws, part, part_auto, p.d_xbuf, s)
+                  : launch<1>(p, d_volts, T, ws, part, part_auto, p.d_xbuf, s);
 }
 
 }  // namespace epic

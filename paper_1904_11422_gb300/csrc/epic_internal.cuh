@@ -86,6 +86,7 @@ struct Plan {
   int ctas_use = 0;  // CTAs an imaging launch may use (0: ctas); set by the batch autotuner
   size_t smem = 0;
   float* d_part = nullptr;      // [ctas][spans][4][N][N]
+  float2* d_xbuf = nullptr;     // N = 128 FP32 path: row exchange between the two CTAs of each cluster
   int* d_part_auto = nullptr;   // [ctas][spans][A][4] exact integer self powers
   size_t device_bytes = 0, workspace_bytes = 0;
 
@@ -137,6 +138,7 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
 // Sets p.threads, p.smem, p.ent_in_smem and returns the co-resident clusters;
 // an imaging launch's WorkSplit then counts clusters.
 size_t fft128_smem_need(int A, int P);
+size_t fft128_xbuf_elems(int clusters, int P);  // float2 of the clusters' exchange buffers
 int fft128_max_ant();
 cudaError_t fft128_config(Plan& p, int* clusters);
 cudaError_t launch_fft128_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
