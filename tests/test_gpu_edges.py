@@ -1,0 +1,95 @@
+"""Edge cases of the 128 x 128 and 32 x 32 paths (FP32 clusters, tensor-core
+parity split and zero-padded transform): single samples, more channels than
+clusters or CTAs, time additivity through accumulate = 1, the host-buffer entry
+point, and the no-allocation entry point's limits."""
+import numpy as np
+import pytest
+
+from paper_1904_11422_gb300 import build_lib, epic, synth
+
+from _helpers import TOL_FP32, assert_close, gpu_image, oracle_image, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fft_fp32": TOL_FP32, "dft_bf16x3": 1e-3, "dft_fp16": 5e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build_lib.build()
+    return epic.load_library()
+
+
+@pytest.mark.parametrize("xf,grid_n", [("fft_fp32", 128), ("dft_bf16x3", 128), ("dft_bf16x3", 32),
+                                       ("dft_fp16", 128)])
+def test_single_sample(xf, grid_n):
+    w = synth.random_small(2101, n_ant=11, n_pol=2, n_chan=3, grid_n=grid_n, support=3, n_time=1)
+    err = rel_errors(gpu_image(w, xform=epic.XFORMS[xf]), oracle_image(w), 2)
+    assert err.max() <= TOL[xf], err.max()
+
+
+@pytest.mark.parametrize("xf,grid_n", [("fft_fp32", 128), ("dft_bf16x3", 128), ("dft_bf16x3", 32)])
+def test_more_channels_than_ctas(xf, grid_n):
+    """Hundreds of channels of two samples each: a CTA (or cluster) spans many
+    channels, and the partial-image slots per CTA are at their largest."""
+    C = 400
+    w = synth.random_small(2102, n_ant=5, n_pol=2, n_chan=C, grid_n=grid_n, support=1, n_time=2,
+                           freq_hz=np.linspace(50e6, 60e6, C))
+    got = gpu_image(w, xform=epic.XFORMS[xf])
+    chans = [0, 1, 199, 398, 399]
+    ref = oracle_image(w, channels=chans)
+    assert rel_errors(got[chans], ref, 2).max() <= TOL[xf]
+    # every channel has the same array and statistics: no channel is left empty
+    assert np.all(np.abs(got[:, 0]).max(axis=(1, 2)) > 0)
+
+
+@pytest.mark.parametrize("xf,grid_n", [("fft_fp32", 128), ("dft_bf16x3", 128), ("dft_bf16x3", 32)])
+def test_time_halves_accumulate(xf, grid_n):
+    import torch
+    w = synth.random_small(2103, n_ant=30, n_pol=2, n_chan=4, grid_n=grid_n, support=5, n_time=37)
+    plan = epic.plan_for(w, epic.XFORMS[xf])
+    dv = torch.from_numpy(w.volts).cuda()
+    whole = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    halves = torch.empty_like(whole)
+    epic.epic_image(plan, dv, w.n_time, whole, 0)
+    epic.epic_image(plan, dv[:20].contiguous(), 20, halves, 0)
+    epic.epic_image(plan, dv[20:].contiguous(), w.n_time - 20, halves, 1)
+    epic.epic_sync(plan)
+    assert rel_errors(halves.cpu().numpy(), whole.cpu().numpy(), 2).max() < 1e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("xf", ["fft_fp32", "dft_bf16x3"])
+def test_host_entry_point_at_128(xf):
+    w = synth.random_small(2104, n_ant=14, n_pol=2, n_chan=2, grid_n=128, support=3, n_time=6)
+    plan = epic.plan_for(w, epic.XFORMS[xf])
+    dev = gpu_image(w, xform=epic.XFORMS[xf], plan=plan)
+    h_out = np.empty(plan.out_shape, np.float32)
+    epic.epic_image_host(plan, np.ascontiguousarray(w.volts), w.n_time, h_out, 0)
+    assert np.array_equal(h_out, dev)
+    plan.close()
+
+
+def test_noalloc_at_128_is_rejected_when_the_workspace_exceeds_the_scratch():
+    import torch
+    w = synth.random_small(2105, n_ant=6, n_pol=2, n_chan=2, grid_n=128, support=3, n_time=3)
+    plan = epic.plan_for(w)
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    dv = torch.from_numpy(w.volts).cuda()
+    if plan.info["workspace_bytes"] > epic.EPIC_NOALLOC_SCRATCH_BYTES:
+        with pytest.raises(epic.EpicError) as ei:
+            epic.epic_image_noalloc(plan, dv, w.n_time, out, 0)
+        assert ei.value.status == epic.EPIC_ERR_UNSUPPORTED
+    else:
+        epic.epic_image_noalloc(plan, dv, w.n_time, out, 0)
+        epic.epic_sync(plan)
+        assert_close(out.cpu().numpy(), oracle_image(w), 2)
+    plan.close()
+
+
+def test_single_antenna_at_128_subtracts_to_zero():
+    for xf in ("fft_fp32", "dft_bf16x3"):
+        w = synth.random_small(2106, n_ant=1, n_pol=2, n_chan=2, grid_n=128, support=5, n_time=5)
+        raw = gpu_image(w, xform=epic.XFORMS[xf], subtract=False)
+        sub = gpu_image(w, xform=epic.XFORMS[xf], subtract=True)
+        assert np.abs(sub).max() <= 1e-5 * np.abs(raw).max(), xf
