@@ -1,5 +1,7 @@
 // epic_api.cu -- the C ABI declared in include/epic.h: validation, plan
 // lifetime, and the launch sequence of one imaging call.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -37,6 +39,13 @@ bool grid_supported(int xform, int N, int P, int A, int S) {
   return (N == 32 || N == 64 || N == 128) && P == 2 && A <= 1024 && epic::dft_smem_need(A, 0) <= kSmemOptin;
 }
 
+// A named range on the profiler's timeline for the life of an entry-point call
+// (NVTX: a no-op unless a profiling tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 epic_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return EPIC_OK;
   if (e == cudaErrorMemoryAllocation) return EPIC_ERR_OOM;
@@ -50,6 +59,7 @@ cudaError_t alloc(T** ptr, size_t count, size_t* total) {
   if (count == 0) return cudaSuccess;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * count);
   if (e == cudaSuccess) *total += sizeof(T) * count;
+  else (void)cudaGetLastError();  // a failed allocation must not be reported again by a later launch
   return e;
 }
 
@@ -223,6 +233,7 @@ epic_status epic_plan_validate(const epic_plan_desc* d) {
 }
 
 epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
+  Range range("epic_plan_create");
   if (!out) return EPIC_ERR_INVALID_ARG;
   *out = nullptr;
   epic_status st = epic_plan_validate(d);
@@ -370,6 +381,7 @@ epic_status epic_plan_query(const epic_plan* h, epic_plan_info* info) {
 
 epic_status epic_image(epic_plan* h, const uint8_t* d_volts, int n_time, float* d_out, int accumulate,
                        void* stream) {
+  Range range("epic_image");
   if (!h || !d_out || n_time < 0 || n_time > (1 << 24) || (accumulate != 0 && accumulate != 1))
     return EPIC_ERR_INVALID_ARG;
   if (n_time > 0 && !d_volts) return EPIC_ERR_INVALID_ARG;
@@ -390,6 +402,7 @@ epic_status epic_image(epic_plan* h, const uint8_t* d_volts, int n_time, float* 
 
 epic_status epic_image_host(epic_plan* h, const uint8_t* h_volts, int n_time, float* h_out, int accumulate,
                             void* stream) {
+  Range range("epic_image_host");
   if (!h || !h_out || n_time < 0 || n_time > (1 << 24) || (accumulate != 0 && accumulate != 1))
     return EPIC_ERR_INVALID_ARG;
   if (n_time > 0 && !h_volts) return EPIC_ERR_INVALID_ARG;
@@ -402,12 +415,18 @@ epic_status epic_image_host(epic_plan* h, const uint8_t* h_volts, int n_time, fl
     p.d_stage_in = nullptr;
     p.stage_in_bytes = 0;
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p.d_stage_in), in_bytes);
-    if (e != cudaSuccess) return from_cuda(e);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return from_cuda(e);
+    }
     p.stage_in_bytes = in_bytes;
   }
   if (!p.d_stage_out) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p.d_stage_out), out_bytes);
-    if (e != cudaSuccess) return from_cuda(e);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return from_cuda(e);
+    }
   }
   cudaError_t e = cudaSuccess;
   if (in_bytes) e = cudaMemcpyAsync(p.d_stage_in, h_volts, in_bytes, cudaMemcpyHostToDevice, s);
@@ -434,6 +453,7 @@ epic_status epic_sync(epic_plan* h, void* stream) {
 
 epic_status epic_grad(epic_plan* h, const uint8_t* d_volts, int n_time, const float* d_gains,
                       const float* d_model, float* d_grad, float* d_loss, void* stream) {
+  Range range("epic_grad");
   if (!h || !d_volts || !d_gains || !d_model || !d_grad || !d_loss || n_time < 1 || n_time > (1 << 24))
     return EPIC_ERR_INVALID_ARG;
   Plan& p = h->p;

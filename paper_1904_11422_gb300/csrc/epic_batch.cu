@@ -7,6 +7,8 @@
 // with a single launch call.  An optional autotuner chooses each plan's CTA
 // count (how many SMs its persistent imaging kernel spreads over, i.e. its
 // time-tile length) by timing candidate graphs.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -202,7 +204,10 @@ epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_
 
 epic_status epic_batch_launch(epic_batch* b, void* stream) {
   if (!b || !b->exec) return EPIC_ERR_INVALID_ARG;
-  return status_of(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)));
+  nvtxRangePushA("epic_batch_launch");
+  const epic_status st = status_of(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)));
+  nvtxRangePop();
+  return st;
 }
 
 epic_status epic_batch_destroy(epic_batch* b) {

@@ -1,7 +1,8 @@
 """Edge cases of the 128 x 128 and 32 x 32 paths (FP32 clusters, tensor-core
 parity split and zero-padded transform): single samples, more channels than
 clusters or CTAs, time additivity through accumulate = 1, the host-buffer entry
-point, and the no-allocation entry point's limits."""
+point, the no-allocation entry point's limits, and host-side fault injection (a
+staging allocation that cannot succeed)."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,24 @@ def test_single_antenna_at_128_subtracts_to_zero():
         raw = gpu_image(w, xform=epic.XFORMS[xf], subtract=False)
         sub = gpu_image(w, xform=epic.XFORMS[xf], subtract=True)
         assert np.abs(sub).max() <= 1e-5 * np.abs(raw).max(), xf
+
+
+def test_failed_staging_allocation_reports_oom_and_the_plan_keeps_working():
+    """Host-side fault injection: a host-buffer call whose staging area (2^24
+    samples of the station block, about 550 GB) cannot be allocated returns
+    EPIC_ERR_OOM without touching the host buffers, and the failed allocation is
+    not reported again by the next call."""
+    import torch
+    w = synth.station(n_time=4, n_chan=64)
+    plan = epic.plan_for(w)
+    h_in = np.zeros(16, np.uint8)
+    h_out = np.empty(plan.out_shape, np.float32)
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_image_host(plan, h_in, 1 << 24, h_out, 0)
+    assert ei.value.status == epic.EPIC_ERR_OOM
+    dv = torch.from_numpy(w.volts).cuda()
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    epic.epic_image(plan, dv, w.n_time, out, 0)
+    epic.epic_sync(plan)
+    assert_close(out.cpu().numpy()[[0, 63]], oracle_image(w, channels=[0, 63]), 2)
+    plan.close()
