@@ -393,6 +393,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     //    completed before its conversion)
     {
       float gre[2][8], gim[2][8];
+      // the entry tables in shared memory or in L2: one inlined copy each, so
+      // that each reads its tables with loads of the right address space
+      auto gather = [&](const uint16_t* EA, const float* EW) {
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         // slot s = cell (s & 1) of pair s >> 1: lane-interleaved entries, warp-uniform trip count
@@ -400,8 +403,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = base_s[warp * 8 + s] + lane;
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
         for (int k = 0; k < K; ++k) {
-          const float w = ent_w[b + 32 * k];
-          const float4 ev = E4[ent_a[b + 32 * k]];
+          const float w = EW[b + 32 * k];
+          const float4 ev = E4[EA[b + 32 * k]];
           xr = fmaf(w, ev.x, xr);
           xi = fmaf(w, ev.y, xi);
           yr = fmaf(w, ev.z, yr);
@@ -409,6 +412,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         gre[0][s] = xr; gim[0][s] = xi; gre[1][s] = yr; gim[1][s] = yi;
       }
+      };
+      if (ent_in_smem)
+        gather(enta_s, entw_s);
+      else
+        gather(ent_a, ent_w);
       if constexpr (Q128) {
         // H_q = exp(+2 pi i (alpha x + beta y) / 128) x the folded gather
         const int alpha = cur_c & 1, beta = (cur_c >> 1) & 1;
