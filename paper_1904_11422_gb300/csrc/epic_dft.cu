@@ -480,58 +480,66 @@ __global__ void __launch_bounds__(kThreads, 1)
       epilogue(prev_buf);
     }
 
-    // 5. Z = D1 -> stage-2 B operand rows (g, k), K = (c, y), split hi/lo; the
-    //    previous sample's stage-2 products, which read this buffer, are complete
+    // 5. Z = D1 -> stage-2 B operand rows (g, k), K = (c, y), split hi/lo (the
+    //    previous sample's stage-2 products, which read this buffer, are
+    //    complete), and 6. stage 2: D2[buf] = Fre . Z^T, lanes (j, c), columns
+    //    (g, k), which runs while the next sample is unpacked and gridded.  Both
+    //    in two halves along K: a thread's first 16 y values are the K steps
+    //    0, 2, 4, 6, its last 16 the steps 1, 3, 5, 7, so the products of the
+    //    first half run while the second half is converted.
     wait_or_abort(bar1, ph1, pend1);
-    {
-      float v[32];
-      const uint32_t d1 = tmem + lane_base + kColD1 + 32 * cq;
-      tmem_ld16(d1, *reinterpret_cast<float(*)[16]>(&v[0]));
-      tmem_ld16(d1 + 16, *reinterpret_cast<float(*)[16]>(&v[16]));
+    uint32_t accum2 = 0;
+    const uint32_t d1 = tmem + lane_base + kColD1 + 32 * cq;
+    const int zrow = cg * kN + ck;
+    auto convert_z = [&](int half) {
+      float v[16];
+      tmem_ld16(d1 + 16 * half, v);
       tmem_wait_ld();
-      const int row = cg * kN + ck;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int qq = 0; qq < 2; ++qq) {
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          hi[h] = pack2<kBf>(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+          hi[h] = pack2<kBf>(v[8 * qq + 2 * h], v[8 * qq + 2 * h + 1]);
           if constexpr (Pr::kSplit) {
             const float2 back = unpack2<kBf>(hi[h]);
-            lo[h] = pack2<kBf>(v[8 * q + 2 * h] - back.x, v[8 * q + 2 * h + 1] - back.y);
+            lo[h] = pack2<kBf>(v[8 * qq + 2 * h] - back.x, v[8 * qq + 2 * h + 1] - back.y);
           }
         }
-        const uint32_t off = slab_off(row, cy0 + 8 * q);
+        const uint32_t off = slab_off(zrow, cy0 + 16 * half + 8 * qq);
         *reinterpret_cast<uint4*>(sm + DftSmem::B2 + cc * kSlab + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         if constexpr (Pr::kSplit)
           *reinterpret_cast<uint4*>(sm + DftSmem::B2 + (2 + cc) * kSlab + off) =
               make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_flag) break;
-
-    // 6. stage 2: D2[buf] = Fre . Z^T, lanes (j, c), columns (g, k); runs while
-    //    the next sample is unpacked and gridded
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t zHi = sbase + DftSmem::B2, zLo = zHi + 2 * kSlab;
-      uint32_t accum = 0;
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+    };
+    auto issue_stage2 = [&](int half) {
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t zHi = sbase + DftSmem::B2, zLo = zHi + 2 * kSlab;
 #pragma unroll
-      for (int pr = 0; pr < (Pr::kSplit ? 3 : 1); ++pr) {
-        const uint32_t fcol = (pr == 1) ? kColFlo : kColFhi;
-        const uint32_t b = (pr == 2) ? zLo : zHi;
+        for (int pr = 0; pr < (Pr::kSplit ? 3 : 1); ++pr) {
+          const uint32_t fcol = (pr == 1) ? kColFlo : kColFhi;
+          const uint32_t b = (pr == 2) ? zLo : zHi;
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          mma_f16_ts(tmem + kColD2 + 128 * d2buf, tmem + fcol + 8 * kk,
-                     sdesc_sw128(b + (kk >> 2) * kSlab + (kk & 3) * 32), kIdesc, accum);
-          accum = 1;
+          for (int kq = 0; kq < 4; ++kq) {
+            const int kk = 2 * kq + half;
+            mma_f16_ts(tmem + kColD2 + 128 * d2buf, tmem + fcol + 8 * kk,
+                       sdesc_sw128(b + (kk >> 2) * kSlab + (kk & 3) * 32), kIdesc, accum2);
+            accum2 = 1;
+          }
         }
+        if (half == 1) mma_commit(bar2);
       }
-      mma_commit(bar2);
-    }
+    };
+    convert_z(0);
+    if (*abort_flag) break;  // no wait lies between here and the commit below
+    issue_stage2(0);
+    convert_z(1);
+    issue_stage2(1);
     have_prev = 1;
     prev_buf = d2buf;
     d2buf ^= 1;
