@@ -321,6 +321,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint16_t* ent_a = enta_s;
   const float* ent_w = entw_s;
 
+  // 1. unpack, calibrate, exact integer self powers of one sample's bytes
+  auto unpack = [&](unsigned rw) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = tid + h * kThreads;
+      const unsigned rb = h ? rw >> 16 : rw & 0xffffu;
+      if (a < A) {
+        const int xr = nib_hi(rb & 0xffu), xi = nib_lo(rb & 0xffu);
+        const int yr = nib_hi(rb >> 8), yi = nib_lo(rb >> 8);
+        const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
+        E4[a] = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
+                            ky.x * yi + ky.y * yr);
+        int4 au = auto_s[a];
+        au.x += xr * xr + xi * xi;
+        au.y += yr * yr + yi * yi;
+        au.z += xr * yr + xi * yi;
+        au.w += xi * yr - xr * yi;
+        auto_s[a] = au;
+      }
+    }
+  };
+  bool have_next = false;  // E already holds this sample (unpacked while stage 1 ran)
   int cur_c = -1;
   for (long long u = u0; u < u1; ++u) {
     const int c = (int)(u / T);
@@ -366,26 +388,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (u + 1 < u1) raw_next = load_raw(u + 1);
 
-    // 1. unpack, calibrate, exact integer self powers
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int a = tid + h * kThreads;
-      const unsigned rb = h ? raw >> 16 : raw & 0xffffu;
-      if (a < A) {
-        const int xr = nib_hi(rb & 0xffu), xi = nib_lo(rb & 0xffu);
-        const int yr = nib_hi(rb >> 8), yi = nib_lo(rb >> 8);
-        const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
-        E4[a] = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
-                            ky.x * yi + ky.y * yr);
-        int4 au = auto_s[a];
-        au.x += xr * xr + xi * xi;
-        au.y += yr * yr + yi * yi;
-        au.z += xr * yr + xi * yi;
-        au.w += xi * yr - xr * yi;
-        auto_s[a] = au;
-      }
+    if (!have_next) {
+      unpack(raw);
+      __syncthreads();
     }
-    __syncthreads();
+    have_next = false;
 
     // 2. grid the thread's four cell pairs (y, 2r..2r+1) of both polarisations
     //    into rows (g, y) of the stage-1 B operand, split into 16-bit hi/lo parts
@@ -474,10 +481,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(bar1);
     }
 
-    // 4. while stage 1 runs: squares of the previous sample
+    // 4. while stage 1 runs: squares of the previous sample, and the next
+    //    sample's fields if it is of the same channel (every thread has
+    //    finished the gather that read E)
     if (have_prev) {
       wait_or_abort(bar2, ph2, pend2);
       epilogue(prev_buf);
+    }
+    if (u + 1 < u1 && (int)((u + 1) / T) == c) {
+      unpack(raw_next);
+      have_next = true;
     }
 
     // 5. Z = D1 -> stage-2 B operand rows (g, k), K = (c, y), split hi/lo (the
