@@ -140,7 +140,9 @@ epic_status epic_plan_query(const epic_plan* plan, epic_plan_info* info);
  *   accumulate 0: d_out = image; 1: d_out += image.
  * With subtract_autos the per-antenna term is removed per call, so images are
  * additive over consecutive blocks.  Deterministic: the same inputs give
- * bit-identical outputs on the same device.  Uses the plan's workspace. */
+ * bit-identical outputs on the same device.  Uses the plan's workspace, so
+ * calls on one plan must be ordered (one stream, or synchronised streams);
+ * different plans may run concurrently. */
 epic_status epic_image(epic_plan* plan, const uint8_t* d_volts, int n_time, float* d_out,
                        int accumulate, void* stream);
 
@@ -235,7 +237,9 @@ typedef struct epic_batch epic_batch;
  * the imaging kernels several times on `stream` and overwrites d_out.
  * chosen_ctas (optional, [n_plans]) receives the CTA caps in the graph.
  * Synchronous.  Results equal epic_image's exactly when tune = 0, and up to the
- * summation order of the partial images (FP32 rounding) when tune = 1. */
+ * summation order of the partial images (FP32 rounding) when tune = 1.  The
+ * graph uses each plan's own workspace: a plan in a batch must not run other
+ * calls (epic_image, epic_grad, another batch) concurrently with a launch. */
 epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_t* const* d_volts,
                               const int* n_time, float* const* d_out, int tune, int* chosen_ctas,
                               void* stream, epic_batch** out);

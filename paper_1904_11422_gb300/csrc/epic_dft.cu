@@ -17,9 +17,16 @@
 // and a low 16-bit part (BF16 or FP16) and three products hi.hi + lo.hi + hi.lo
 // are accumulated (the "x3" transforms), or only the high parts are used.
 //
+// The transform is always the 64-point one: a 128 x 128 grid runs as four 64 x 64
+// problems of parity-folded fields (see Q128 below), a 32 x 32 grid as the 64 x 64
+// transform of the zero-padded grid whose even output pixels are kept (done by
+// the gather tables and the reduction; the kernel is the same).
+//
 // The samples of a CTA are software-pipelined: the stage-2 products of sample t
-// run while sample t+1 is unpacked and gridded, and the stage-1 products of t+1
-// run while sample t is squared and accumulated.
+// run while sample t+1 is unpacked and gridded (the first half of them already
+// while the second half of Z is converted), the stage-1 products of t+1 run while
+// sample t is squared and accumulated, and sample t+2's fields are unpacked while
+// stage 1 of t+1 runs.
 //
 // One elected thread issues the MMAs and commits them to mbarriers; every wait
 // on them is bounded (about one second) and reports EPIC_ERR_TIMEOUT through the
