@@ -28,10 +28,22 @@ double cell_coord(double pos_m, double freq_hz, double cell_lambda, int N) {
 
 constexpr size_t kSmemOptin = 232448;  // opt-in shared memory per CTA on sm_100/sm_103 (227 KB)
 
+// FP32 path on 128 x 128 grids: four folded 64 x 64 problems per channel run by
+// the 64 x 64 kernel, or clusters of two CTAs that split one 128 x 128 problem.
+// Folding repeats the gather four times but runs the cheaper 64 x 64 transforms;
+// measured on the station array (A S^2 = 6 400 entries per channel) folding took
+// 10.3 ms against 11.5 ms, on 1 024 antennas (25 600 entries) 10.4 ms against
+// 8.2 ms, which puts the crossover near 10 000 entries per channel.  Arrays too
+// large for the clusters are always folded.
+bool fft128_fold(int A, int S) {
+  return (long long)A * S * S <= 10000 || A > epic::fft128_max_ant() ||
+         epic::fft128_smem_need(A, 2) > kSmemOptin;
+}
+
 bool grid_supported(int xform, int N, int P, int A, int S) {
   if (xform == EPIC_XFORM_FFT_FP32) {
-    if (N == 128) return A <= epic::fft128_max_ant() && epic::fft128_smem_need(A, P) <= kSmemOptin;
-    return (N == 32 || N == 64) && A <= kMaxAntFft;
+    if (N == 128 && !fft128_fold(A, S)) return A <= epic::fft128_max_ant() && epic::fft128_smem_need(A, P) <= kSmemOptin;
+    return (N == 32 || N == 64 || N == 128) && A <= kMaxAntFft;
   }
   // tensor path: 64 x 64 or 128 x 128 grids of two polarisations, up to 1024
   // antennas (gather entries in shared memory when they fit, else read from L2)
@@ -308,7 +320,12 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   int per_sm = 0;
   size_t gt_bytes = 0;
   int clusters = 0;  // N = 128: the imaging launch counts clusters of two CTAs
-  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128) {
+  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128 && fft128_fold(p.A, p.S)) {
+    p.vq = 4;
+    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft64Q, 512, 0, &gt_bytes));
+    total += gt_bytes;
+    EPIC_TRY(epic::fft_image_config(p, &per_sm));
+  } else if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128) {
     EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft128, 1024, 0, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(epic::fft128_config(p, &clusters));
@@ -338,7 +355,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   const size_t Ns = p.vq == 4 ? N / 2 : N * p.dec;  // side of a partial image
   EPIC_TRY(alloc(&p.d_part, (size_t)p.ctas * p.spans * 4 * Ns * Ns, &total));
   EPIC_TRY(alloc(&p.d_part_auto, (size_t)p.ctas * p.spans * A * 4, &total));
-  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128)
+  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128 && p.vq == 1)
     EPIC_TRY(alloc(&p.d_xbuf, epic::fft128_xbuf_elems(p.ctas, p.P), &total));
   p.workspace_bytes = total - before;
   // epic_grad: FP32 FFT plans of 64 x 64 grids with one antenna per thread

@@ -135,7 +135,14 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int e
   return L;
 }
 
-template <int N, int P>
+// Q (N = 64 only): a 128 x 128 grid run as four 64 x 64 problems, virtual
+// channel 4 c + q per output-parity subset q = alpha + 2 beta: the gather tables
+// fold the four quadrants with signed weights (layout kFft64Q), each gathered
+// cell (y, x) is multiplied by exp(+2 pi i (alpha x + beta y) / 128), and the
+// reduction interleaves the four 64 x 64 partial images (pixel (j, i) of subset
+// q is pixel (2 j + beta, 2 i + alpha)).  `twiddle` then holds the 128-point
+// table, `C` the real channel count.
+template <int N, int P, bool Q = false>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     fft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
   float2 tw[8];
   tw[0] = make_float2(1.f, 0.f);
 #pragma unroll
-  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[(n1 * k2) & (N - 1)];
+  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[Q ? ((n1 * k2) & (N - 1)) * 2 : (n1 * k2) & (N - 1)];
 
   const long long u0 = (long long)blockIdx.x * W;
   const long long u1 = min(u0 + W, units);
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
   // raw bytes of the thread's antennas, prefetched one unit ahead
   unsigned raw[MAXK] = {}, raw_next[MAXK] = {};
   auto load_raw = [&](long long u, unsigned (&dst)[MAXK]) {
-    const int c = (int)(u / T), t = (int)(u % T);
+    const int c = (int)(u / T) >> (Q ? 2 : 0), t = (int)(u % T);
     const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
 #pragma unroll
     for (int k = 0; k < MAXK; ++k) {
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
         cnt_s[tid] = g_cnt[(size_t)c * WARPS * 8 + tid];
         base_s[tid] = g_base[(size_t)c * WARPS * 8 + tid];
       }
-      for (int k = tid; k < A * P; k += NT) coef_s[k] = coef[(size_t)c * A * P + k];
+      for (int k = tid; k < A * P; k += NT) coef_s[k] = coef[(size_t)(c >> (Q ? 2 : 0)) * A * P + k];
       for (int a = tid; a < A; a += NT) auto_s[a] = make_int4(0, 0, 0, 0);
       const int e0 = g_off[c], ne = g_off[c + 1] - e0;
       if (ent_in_smem) {
@@ -303,6 +310,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
             gx.y = fmaf(w1, e1.y, fmaf(w0, e0.y, gx.y));
           }
         }
+        if constexpr (Q) {
+          // H_q = exp(+2 pi i (alpha x + beta y) / 128) x the folded gather
+          const float2 w = __ldg(twiddle + (((cur_c & 1) * (n1 + R1 * n2) + ((cur_c >> 1) & 1) * y) & 127));
+          gx = make_float2(gx.x * w.x - gx.y * w.y, gx.x * w.y + gx.y * w.x);
+          gy = make_float2(gy.x * w.x - gy.y * w.y, gy.x * w.y + gy.y * w.x);
+        }
         v[0][n2] = gx;
         if constexpr (P == 2) v[1][n2] = gy;
       }
@@ -351,13 +364,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 template <int N, int P>
 cudaError_t occupancy(int threads, size_t smem, int* per_sm) {
   cudaError_t e = allow_max_smem(fft_image_kernel<N, P>);
+  if (e == cudaSuccess && N == 64) e = allow_max_smem(fft_image_kernel<64, P, true>);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fft_image_kernel<N, P>, threads, smem);
 }
 
 size_t smem_for(const Plan& p, int ent_in_smem) {
   const int me = p.gt.max_chan_entries;
-  if (p.N == 64) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem).total
+  if (p.N == 64 || p.vq == 4) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem).total
                                  : fft_smem_layout<64, 1>(p.A, me, ent_in_smem).total;
   return p.P == 2 ? fft_smem_layout<32, 2>(p.A, me, ent_in_smem).total
                   : fft_smem_layout<32, 1>(p.A, me, ent_in_smem).total;
@@ -407,14 +421,26 @@ __global__ void debug_grid_kernel(const uint8_t* __restrict__ volts, int T, int 
 cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
   p.ent_in_smem = ent_fits(p) ? 1 : 0;
   p.smem = smem_for(p, p.ent_in_smem);
-  p.threads = (p.N == 64) ? Geo<64>::THREADS : Geo<32>::THREADS;
-  if (p.N == 64) return p.P == 2 ? occupancy<64, 2>(p.threads, p.smem, ctas_per_sm)
+  const bool n64 = p.N == 64 || p.vq == 4;  // 128 x 128 grids folded into 64 x 64 problems
+  p.threads = n64 ? Geo<64>::THREADS : Geo<32>::THREADS;
+  if (n64) return p.P == 2 ? occupancy<64, 2>(p.threads, p.smem, ctas_per_sm)
                                  : occupancy<64, 1>(p.threads, p.smem, ctas_per_sm);
   return p.P == 2 ? occupancy<32, 2>(p.threads, p.smem, ctas_per_sm)
                   : occupancy<32, 1>(p.threads, p.smem, ctas_per_sm);
 }
 
 cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s) {
+  if (p.N == 128 && p.vq == 4) {  // four folded 64 x 64 problems per channel
+    if (p.P == 2)
+      fft_image_kernel<64, 2, true><<<ws.ctas, p.threads, p.smem, s>>>(
+          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, p.d_part, p.d_part_auto);
+    else
+      fft_image_kernel<64, 1, true><<<ws.ctas, p.threads, p.smem, s>>>(
+          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, p.d_part, p.d_part_auto);
+    return cudaGetLastError();
+  }
   if (p.N == 128) return launch_fft128_image_ws(p, d_volts, T, ws, p.d_part, p.d_part_auto, s);
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \
@@ -432,6 +458,17 @@ cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkS
 
 cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                                 int* part_auto, cudaStream_t s) {
+  if (p.N == 128 && p.vq == 4) {  // four folded 64 x 64 problems per channel
+    if (p.P == 2)
+      fft_image_kernel<64, 2, true><<<ws.ctas, p.threads, p.smem, s>>>(
+          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
+    else
+      fft_image_kernel<64, 1, true><<<ws.ctas, p.threads, p.smem, s>>>(
+          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
+    return cudaGetLastError();
+  }
   if (p.N == 128) return launch_fft128_image_ws(p, d_volts, T, ws, part, part_auto, s);
   const int ent = p.ent_in_smem;
 #define EPIC_LAUNCH(NN_, PP_)                                                                                   \

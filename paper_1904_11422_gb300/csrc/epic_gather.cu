@@ -27,6 +27,8 @@
 //           (-1)^(alpha s + beta u) (alpha = q & 1, beta = q >> 1); its entry
 //           list is the four cells' lists in (u, s) order, weights signed.  One
 //           table set per virtual channel 4 c + q.
+//   kFft64Q: the kFft64 row layout over the folded fields H_q (the FP32 path's
+//           128 x 128 grids run as four 64 x 64 problems), trip counts even.
 //   kPairD: the same over a 64 x 64 field holding a 32 x 32 grid in its cells
 //           y, x < 32 (zero elsewhere): the tensor path's transform of 32 x 32
 //           grids, whose even output pixels are the 32-point transform.
@@ -42,6 +44,7 @@ namespace {
 __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
   switch (layout) {
     case kLayoutFft64:
+    case kLayoutFft64Q:
     case kLayoutFft128: return make_int2(task >> 3, (task & 7) + 8 * s);
     case kLayoutFft32: return make_int2(task >> 2, (task & 3) + 4 * s);
     default: return make_int2(task >> 3, 8 * (task & 7) + s);
@@ -49,16 +52,16 @@ __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
 }
 
 // Grid cell of field cell (y, x), or -1 where the field is zero (kLayoutPairD
-// outside the 32 x 32 grid); not used by kLayoutPairQ.
+// outside the 32 x 32 grid); not used by the folded layouts.
 __device__ __forceinline__ int field_cell(int layout, int N, int y, int x) {
   if (layout == kLayoutPairD) return (y < N && x < N) ? y * N + x : -1;
   return y * N + x;
 }
 
-// Entries of cell (y, x) of the gathered field: a grid cell, or for kLayoutPairQ
+// Entries of cell (y, x) of the gathered field: a grid cell, or for a folded layout
 // the four grid cells folded into H_q(y, x).
 __device__ __forceinline__ int field_count(int layout, const int* ptr, int N, int y, int x) {
-  if (layout != kLayoutPairQ) {
+  if (!layout_folded(layout)) {
     const int cell = field_cell(layout, N, y, x);
     return cell < 0 ? 0 : ptr[cell + 1] - ptr[cell];
   }
@@ -111,8 +114,8 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   int* pair_of = perm + (pairs ? 2048 : nt);  // [4 nt] (pairs only)
   // table set (channel, or virtual channel 4 c + q) and the grid channel it reads
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int cg = layout == kLayoutPairQ ? c >> 2 : c;
-  const int alpha = c & 1, beta = (c >> 1) & 1;  // kLayoutPairQ only
+  const int cg = layout_folded(layout) ? c >> 2 : c;
+  const int alpha = c & 1, beta = (c >> 1) & 1;  // folded layouts only
   const int* ptr = csr_ptr + (size_t)cg * (N * N + 1);
 
   int task = tid;
@@ -127,7 +130,7 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
     int key = 0;
     for (int s = 0; s < ns; ++s) {
       const int2 yx = cell_of(layout, tid, s);
-      key += ptr[yx.x * N + yx.y + 1] - ptr[yx.x * N + yx.y];
+      key += field_count(layout, ptr, N, yx.x, yx.y);
     }
     if (sorted) {
       keys[tid] = key;
@@ -143,13 +146,15 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   int cnt[16], beg[16];
   for (int s = 0; s < ns; ++s) {
     const int2 yx = cells[s];
-    const int cell = layout == kLayoutPairQ ? -1 : field_cell(layout, N, yx.x, yx.y);
+    const int cell = layout_folded(layout) ? -1 : field_cell(layout, N, yx.x, yx.y);
     beg[s] = cell < 0 ? 0 : ptr[cell];
     cnt[s] = field_count(layout, ptr, N, yx.x, yx.y);
     // FFT layouts: trip count rounded up to even (that kernel walks entries in pairs)
     const int kmax = __reduce_max_sync(0xffffffffu, cnt[s]);
-    const int k = (layout == kLayoutFft64 || layout == kLayoutFft32 || layout == kLayoutFft128) ? ((kmax + 1) & ~1)
-                                                                                                : kmax;
+    const int k = (layout == kLayoutFft64 || layout == kLayoutFft32 || layout == kLayoutFft128 ||
+                   layout == kLayoutFft64Q)
+                      ? ((kmax + 1) & ~1)
+                      : kmax;
     if (lane == 0) kws[w * ns + s] = k;
   }
   __syncthreads();
@@ -176,7 +181,7 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   const int2* ent = csr_ent + (size_t)cg * nnz;
   for (int s = 0; s < ns; ++s) {
     const int K = kws[w * ns + s];
-    if (layout == kLayoutPairQ) {
+    if (layout_folded(layout)) {
       // the four source cells' entries in (u, s) order, weights signed, then padding
       int k = 0;
       for (int us = 0; us < 4; ++us) {
@@ -223,7 +228,7 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   const int ns = layout == kLayoutFft128 ? 16 : 8;
   const int nnz = p.A * p.S * p.S;
   const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
-  const int nsets = layout == kLayoutPairQ ? 4 * p.C : p.C;  // table sets (virtual channels)
+  const int nsets = layout_folded(layout) ? 4 * p.C : p.C;  // table sets (virtual channels)
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
                                      (pairs ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));
   int* d_tot = nullptr;

@@ -40,7 +40,10 @@ struct WorkSplit {
 
 // Gather tables of a gridder (see epic_gather.cu).
 enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3, kLayoutFft128 = 4,
-             kLayoutPairQ = 5, kLayoutPairD = 6 };
+             kLayoutPairQ = 5, kLayoutPairD = 6, kLayoutFft64Q = 7 };
+// Layouts whose table set 4 c + q gathers the 128 x 128 grid of channel c folded
+// into the 64 x 64 field H_q of output-parity subset q.
+__host__ __device__ inline bool layout_folded(int layout) { return layout == kLayoutPairQ || layout == kLayoutFft64Q; }
 struct GatherTables {
   int layout = 0, threads = 0, sorted = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel

@@ -62,7 +62,8 @@ extern "C" epic_status epic_image_noalloc(epic_plan* h, const uint8_t* d_volts, 
   if (e != cudaSuccess) return status_of(e);
   if (dev != p.device) return EPIC_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t part_bytes = align256(sizeof(float) * (size_t)p.ctas * p.spans * 4 * p.N * p.N);
+  const size_t Ns = p.vq == 4 ? p.N / 2 : (size_t)p.N * p.dec;  // side of a partial image
+  const size_t part_bytes = align256(sizeof(float) * (size_t)p.ctas * p.spans * 4 * Ns * Ns);
   const size_t auto_bytes = align256(sizeof(int) * (size_t)p.ctas * p.spans * p.A * 4);
   if (part_bytes + auto_bytes > (size_t)EPIC_NOALLOC_SCRATCH_BYTES) return EPIC_ERR_UNSUPPORTED;
   const size_t out_n = (size_t)p.C * 4 * p.N * p.N;
@@ -72,7 +73,7 @@ extern "C" epic_status epic_image_noalloc(epic_plan* h, const uint8_t* d_volts, 
   // both entry points sum in the same order.
   epic::WorkSplit ws;
   ws.T = n_time;
-  ws.units = (long long)p.C * n_time;
+  ws.units = (long long)p.C * p.vq * n_time;
   const long long ctas = p.ctas < ws.units ? p.ctas : ws.units;
   ws.W = (ws.units + ctas - 1) / ctas;
   ws.ctas = (int)((ws.units + ws.W - 1) / ws.W);

@@ -137,11 +137,12 @@ def test_no_cpu_fallback(tmp_path):
 
 
 def test_validate_antenna_limits_per_grid(lib):
-    """The FP32 path takes up to 2048 antennas on 32 / 64 grids and up to 1024
-    on 128 x 128 grids (whose clusters keep every antenna's field in shared
-    memory next to half of the grid)."""
+    """The FP32 path takes up to 2048 antennas on every grid size (128 x 128
+    grids of large arrays run on clusters, the others as four folded 64 x 64
+    problems)."""
     rng = np.random.default_rng(5)
-    for n_ant, grid_n, code in [(1024, 128, epic.EPIC_OK), (1025, 128, epic.EPIC_ERR_UNSUPPORTED),
+    for n_ant, grid_n, code in [(1024, 128, epic.EPIC_OK), (1025, 128, epic.EPIC_OK),
+                                (2048, 128, epic.EPIC_OK), (2049, 128, epic.EPIC_ERR_UNSUPPORTED),
                                 (2048, 64, epic.EPIC_OK), (2049, 64, epic.EPIC_ERR_UNSUPPORTED)]:
         ant = (rng.random((n_ant, 2)) - 0.5) * 20.0  # within a few cells of the centre at 50 MHz
         d, keep = epic.make_desc(ant, [50e6], 2, grid_n, 3)

@@ -115,3 +115,10 @@ def test_failed_staging_allocation_reports_oom_and_the_plan_keeps_working():
     epic.epic_sync(plan)
     assert_close(out.cpu().numpy()[[0, 63]], oracle_image(w, channels=[0, 63]), 2)
     plan.close()
+
+
+def test_grid128_fold_beyond_the_cluster_limit():
+    """1500 antennas on a 128 x 128 grid: more than the clusters take, so the
+    channel runs as four folded 64 x 64 problems."""
+    w = synth.random_small(2107, n_ant=1500, n_pol=2, n_chan=2, grid_n=128, support=1, n_time=3)
+    assert_close(gpu_image(w), oracle_image(w), 2)
