@@ -270,8 +270,12 @@ def time_grid128(args, epic, synth, torch, stream, world, shard, sms, pk, pk_kin
         if xf == "fft_fp32":
             flops = w.n_chan * w.n_time * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
             peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"bound": "alu", "kernel": "fft128_image (2-CTA clusters)",
-                    "traffic": dram_traffic("fft128_image", "epic_fft128.cu"),
+            clustered = plan.info["cluster_dim"] == 2
+            roof = {"bound": "alu",
+                    "kernel": ("fft128_image (2-CTA clusters)" if clustered else
+                               "fft_image (each image set as four folded 64x64 problems)"),
+                    "traffic": (dram_traffic("fft128_image", "epic_fft128.cu") if clustered else
+                                dram_traffic("fft_image_128fold", "epic_fft.cu")),
                     "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind})"}
         else:

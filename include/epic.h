@@ -99,6 +99,12 @@ typedef struct {
   size_t device_bytes;       /* device memory held by the plan                   */
   size_t workspace_bytes;    /* of which per-call scratch (partial images)       */
   long long max_time;        /* largest n_time accepted by one epic_image call   */
+  int cluster_dim;           /* CTAs per thread-block cluster of the imaging launch
+                                (2: a 128 x 128 grid split over two SMs), else 1  */
+  int transform_n;           /* side of the 2-D transforms the imaging kernel runs */
+  int transforms_per_image;  /* transforms per (sample, channel, polarisation):
+                                4 when a 128 x 128 grid is folded into 64 x 64
+                                parity problems, else 1                          */
 } epic_plan_info;
 
 /* Host-only check of a descriptor, no CUDA call (the same checks that

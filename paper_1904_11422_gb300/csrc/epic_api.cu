@@ -393,6 +393,9 @@ epic_status epic_plan_query(const epic_plan* h, epic_plan_info* info) {
   info->workspace_bytes = p.workspace_bytes;
   // integer self powers stay exact in int32 per CTA and the unit index in int64
   info->max_time = (1LL << 24);
+  info->cluster_dim = (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128 && p.vq == 1) ? 2 : 1;
+  info->transform_n = p.vq == 4 ? p.N / 2 : (p.xform != EPIC_XFORM_FFT_FP32 ? 64 : p.N);
+  info->transforms_per_image = p.vq;
   return EPIC_OK;
 }
 
