@@ -59,43 +59,65 @@ __global__ void loss_sum_kernel(int C, const double* __restrict__ loss_part, flo
 }
 
 // Final gradient per (c, a, p): CTA sums of the data term in CTA order (FP64),
-// minus the autocorrelation term, times 2.  One block per channel, one thread
-// per antenna.
-__global__ void grad_reduce_kernel(int T, int A, int P, int N, long long W, int ctas, int spans, int subtract,
-                                   const float2* __restrict__ gpart, const int* __restrict__ part_auto,
-                                   const float* __restrict__ resid, const float* __restrict__ kx2,
-                                   const float* __restrict__ ky2, const float* __restrict__ gains,
-                                   float* __restrict__ grad) {
-  const int c = blockIdx.x, NN = N * N;
+// minus the autocorrelation term, times 2.  Block (c, group of 8 antennas), one
+// warp per antenna; the channel's residual planes are staged in shared memory
+// (row stride N + 1, so the lanes' rows fall in different banks).  For
+// S = sum_pix R |W_a|^2 = sum_j |FT w_y(j)|^2 sum_i R[j][i] |FT w_x(i)|^2 the lanes
+// take rows j = lane, lane + 32, ... (each row sum in FP32 in column order), and
+// the warp adds |FT w_y(j)| x row in FP64.
+constexpr int kGradAntPerBlock = 8;
+__global__ void __launch_bounds__(32 * kGradAntPerBlock)
+    grad_reduce_kernel(int T, int A, int P, int N, long long W, int ctas, int spans, int subtract,
+                       const float2* __restrict__ gpart, const int* __restrict__ part_auto,
+                       const float* __restrict__ resid, const float* __restrict__ kx2,
+                       const float* __restrict__ ky2, const float* __restrict__ gains,
+                       float* __restrict__ grad) {
+  extern __shared__ float Rs[];  // [P][N][N + 1]
+  const int c = blockIdx.x, NN = N * N, ld = N + 1;
+  if (subtract)
+    for (int k = threadIdx.x; k < P * NN; k += blockDim.x) {
+      const int p = k / NN, j = (k % NN) / N, i = k % N;
+      Rs[(p * N + j) * ld + i] = resid[((size_t)c * 2 + p) * NN + j * N + i];
+    }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = blockIdx.y * kGradAntPerBlock + warp;
+  if (a >= A) return;
   const long long b_lo = ((long long)c * T) / W;
   const long long b_hi = min(((long long)(c + 1) * T - 1) / W, (long long)ctas - 1);
-  for (int a = threadIdx.x; a < A; a += blockDim.x) {
-    double dr[2] = {0.0, 0.0}, di[2] = {0.0, 0.0};
-    long long pw[2] = {0, 0};
-    for (long long b = b_lo; b <= b_hi; ++b) {
-      const int slot = c - (int)((b * W) / T);
-      for (int p = 0; p < P; ++p) {
-        const float2 v = gpart[((size_t)(b * spans + slot) * A + a) * P + p];
-        dr[p] += v.x;
-        di[p] += v.y;
-      }
-      const int4 q = reinterpret_cast<const int4*>(part_auto)[(b * spans + slot) * A + a];
-      pw[0] += q.x;
-      pw[1] += q.y;
+  double dr[2] = {0.0, 0.0}, di[2] = {0.0, 0.0};
+  long long pw[2] = {0, 0};
+  for (long long b = b_lo; b <= b_hi; ++b) {
+    const int slot = c - (int)((b * W) / T);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      if (p >= P) break;
+      const float2 v = gpart[((size_t)(b * spans + slot) * A + a) * P + p];
+      dr[p] += v.x;
+      di[p] += v.y;
     }
-    for (int p = 0; p < P; ++p) {
+    const int4 q = reinterpret_cast<const int4*>(part_auto)[(b * spans + slot) * A + a];
+    pw[0] += q.x;
+    pw[1] += q.y;
+  }
+  const float* kx = kx2 + ((size_t)c * A + a) * N;
+  const float* ky = ky2 + ((size_t)c * A + a) * N;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (p >= P) break;
+    double S = 0.0;
+    if (subtract) {
+      for (int j = lane; j < N; j += 32) {
+        const float* Rj = Rs + (p * N + j) * ld;
+        float row = 0.f;
+        for (int i = 0; i < N; ++i) row = fmaf(Rj[i], __ldg(kx + i), row);
+        S += (double)__ldg(ky + j) * (double)row;
+      }
+      for (int off = 16; off > 0; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
+    }
+    if (lane == 0) {
       double ar = 0.0, ai = 0.0;
       if (subtract) {
-        // S = sum_pix R |W_a|^2 = sum_j |FT w_y(j)|^2 sum_i R[j][i] |FT w_x(i)|^2
-        const float* R = resid + ((size_t)c * 2 + p) * NN;
-        const float* kx = kx2 + ((size_t)c * A + a) * N;
-        const float* ky = ky2 + ((size_t)c * A + a) * N;
-        double S = 0.0;
-        for (int j = 0; j < N; ++j) {
-          float row = 0.f;
-          for (int i = 0; i < N; ++i) row = fmaf(R[j * N + i], kx[i], row);
-          S += (double)ky[j] * (double)row;
-        }
         const double gr = gains[2 * (((size_t)c * A + a) * P + p)], gi = gains[2 * (((size_t)c * A + a) * P + p) + 1];
         ar = gr * (double)pw[p] * S;
         ai = gi * (double)pw[p] * S;
@@ -125,8 +147,15 @@ cudaError_t launch_residual(Plan& p, const float* d_model, float* d_loss, cudaSt
 
 cudaError_t launch_grad_reduce(Plan& p, int T, const WorkSplit& ws, const float* d_gains, float* d_grad,
                                cudaStream_t s) {
-  grad_reduce_kernel<<<p.C, 256, 0, s>>>(T, p.A, p.P, p.N, ws.W, ws.ctas, ws.spans, p.subtract, p.d_gpart,
-                                         p.d_part_auto, p.d_resid, p.d_kx2, p.d_ky2, d_gains, d_grad);
+  const size_t smem = p.subtract ? sizeof(float) * (size_t)p.P * p.N * (p.N + 1) : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_max_smem(grad_reduce_kernel);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(p.C, (p.A + kGradAntPerBlock - 1) / kGradAntPerBlock);
+  grad_reduce_kernel<<<grid, 32 * kGradAntPerBlock, smem, s>>>(T, p.A, p.P, p.N, ws.W, ws.ctas, ws.spans,
+                                                               p.subtract, p.d_gpart, p.d_part_auto, p.d_resid,
+                                                               p.d_kx2, p.d_ky2, d_gains, d_grad);
   return cudaGetLastError();
 }
 
