@@ -10,8 +10,6 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
-#include <cstdio>
-#include <cstdlib>
 #include <new>
 #include <vector>
 
@@ -35,7 +33,6 @@ namespace {
 
 epic_status status_of(cudaError_t e) {
   if (e == cudaSuccess) return EPIC_OK;
-  if (std::getenv("EPIC_DEBUG")) std::fprintf(stderr, "epic_batch: %s\n", cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return EPIC_ERR_OOM;
   return EPIC_ERR_CUDA;
 }
