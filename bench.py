@@ -53,6 +53,8 @@ def parse():
                     help="further transforms timed the same way and reported under 'paths' ('' for none)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="CPU time budget of the whole --impl reference run")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--soak-seconds", type=float, default=1.5)
     ap.add_argument("--grid128-steps", type=int, default=20,
@@ -207,7 +209,7 @@ def run_reference(args):
         return 0
     from paper_1904_11422_gb300 import synth
     w = synth.station()
-    budget = 150.0  # seconds for the whole reference run
+    budget = args.ref_seconds  # seconds for the whole reference run
     per_step = max(0.2, budget / max(1, args.steps + args.warmup))
     oracle, arr, cores = _oracle_setup(w)
     n_c, n_t, _ = _oracle_sample(oracle, arr, w, cores, per_step)
