@@ -148,18 +148,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def strip_comments(src):
+    """C/CUDA source without its comments and with whitespace runs collapsed:
+    edits to comments or layout leave it unchanged, any change to the code does
+    not."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        ch = src[i]
+        if ch in "\"'":  # a string or character literal, copied whole
+            j = i + 1
+            while j < n and src[j] != ch:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(ch)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def src_sha(name):
-    with open(os.path.join(ROOT, "paper_1904_11422_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of a kernel source's code (comments and layout excluded), which keys
+    the ncu traffic figures taken on it."""
+    with open(os.path.join(ROOT, "paper_1904_11422_gb300", "csrc", name), encoding="utf-8") as f:
+        return hashlib.sha256(strip_comments(f.read()).encode()).hexdigest()[:16]
 
 
-def dram_traffic(kernel, source):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source is unchanged since it was taken; else None."""
+def dram_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the code of the
+    kernel's source file is unchanged since it was taken; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             rec = json.load(f).get(kernel)
-        if rec and rec.get("source_sha") == src_sha(source):
+        if rec and rec.get("source_sha") == src_sha(rec["source"]):
             return rec["bytes_per_launch"]
     except Exception:
         pass
@@ -276,15 +304,15 @@ def time_grid128(args, epic, synth, torch, stream, world, shard, sms, pk, pk_kin
             roof = {"bound": "alu",
                     "kernel": ("fft128_image (2-CTA clusters)" if clustered else
                                "fft_image (each image set as four folded 64x64 problems)"),
-                    "traffic": (dram_traffic("fft128_image", "epic_fft128.cu") if clustered else
-                                dram_traffic("fft_image_128fold", "epic_fft.cu")),
+                    "traffic": (dram_traffic("fft128_image") if clustered else
+                                dram_traffic("fft_image_128fold")),
                     "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind})"}
         else:
             flops = w.n_chan * w.n_time * 4 * tensor_flops_per_tc(xf)
             peak = pk.get("bf16_tflops", 1900.0)
             roof = {"bound": "tensor", "kernel": "dft_image (4 parity sub-problems of 64x64 per image set)",
-                    "traffic": dram_traffic("dft_image_128", "epic_dft.cu") if xf == "dft_bf16x3" else None,
+                    "traffic": dram_traffic("dft_image_128") if xf == "dft_bf16x3" else None,
                     "peak_basis": f"measured dense BF16 cuBLAS burst ({pk_kind})",
                     "useful_tflops": flops / (3 if xf.endswith("x3") else 1) / avg_s / 1e12}
         roof.update({"achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -432,14 +460,14 @@ def main():
             flops = w.n_chan * T * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support)
             peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "traffic": dram_traffic("fft_image", "epic_fft.cu"), "kernel": dom,
+                    "traffic": dram_traffic("fft_image"), "kernel": dom,
                     "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
                                   f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz (max SM clock, {pk_kind})"}
         else:
             flops = w.n_chan * T * tensor_flops_per_tc(xf)
             peak = pk.get("bf16_tflops", 1900.0)
             roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "traffic": dram_traffic("dft_image", "epic_dft.cu"), "kernel": dom,
+                    "traffic": dram_traffic("dft_image"), "kernel": dom,
                     "peak_basis": f"measured dense BF16 cuBLAS burst ({pk_kind}); FP16 dense rate taken equal",
                     "useful_tflops": flops / (3 if xf.endswith("x3") else 1) / avg_s / 1e12}
         roof["frac"] = roof["achieved"] / roof["peak"]

@@ -23,3 +23,35 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_source_hash_ignores_comments_but_not_code():
+    b = _bench()
+    code = 'int f(int a) { return a + 1; }  // adds one\nconst char* s = "// kept";\n'
+    assert b.strip_comments(code) == b.strip_comments("/* doc */ int f(int a)\n{ return a + 1; }\n"
+                                                      'const char* s = "// kept";')
+    assert b.strip_comments(code) != b.strip_comments(code.replace("a + 1", "a + 2"))
+    assert '"// kept"' in b.strip_comments(code)
+
+
+def test_traffic_records_are_reported_only_for_the_code_they_were_taken_on():
+    """Each ncu traffic record names its summary and its kernel source; the
+    benchmark reports its bytes while the source's code hash matches the
+    recorded one and null once the kernel has changed."""
+    b = _bench()
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+        recs = json.load(f)
+    assert {"fft_image", "dft_image"} <= set(recs)
+    for name, rec in recs.items():
+        assert rec["bytes_per_launch"] == rec["read_bytes"] + rec["write_bytes"], name
+        assert os.path.exists(os.path.join(ROOT, rec["summary"])), name
+        current = rec["source_sha"] == b.src_sha(rec["source"])
+        assert b.dram_traffic(name) == (rec["bytes_per_launch"] if current else None), name
