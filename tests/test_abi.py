@@ -147,3 +147,18 @@ def test_validate_antenna_limits_per_grid(lib):
         ant = (rng.random((n_ant, 2)) - 0.5) * 20.0  # within a few cells of the centre at 50 MHz
         d, keep = epic.make_desc(ant, [50e6], 2, grid_n, 3)
         assert epic.epic_plan_validate(d) == code, (n_ant, grid_n)
+
+
+def test_validate_antenna_limits_small_grid_and_tensor_path(lib):
+    """2048 antennas on the FP32 path at 32 x 32 as well; 1024 on the tensor path
+    at every grid side it takes."""
+    rng = np.random.default_rng(6)
+    cases = [(2048, 32, epic.EPIC_XFORM_FFT_FP32, epic.EPIC_OK),
+             (2049, 32, epic.EPIC_XFORM_FFT_FP32, epic.EPIC_ERR_UNSUPPORTED)]
+    for grid_n in (32, 64, 128):
+        cases += [(1024, grid_n, epic.EPIC_XFORM_DFT_BF16X3, epic.EPIC_OK),
+                  (1025, grid_n, epic.EPIC_XFORM_DFT_BF16X3, epic.EPIC_ERR_UNSUPPORTED)]
+    for n_ant, grid_n, xf, code in cases:
+        ant = (rng.random((n_ant, 2)) - 0.5) * 20.0
+        d, keep = epic.make_desc(ant, [50e6], 2, grid_n, 3, xform=xf)
+        assert epic.epic_plan_validate(d) == code, (n_ant, grid_n, xf)
