@@ -53,6 +53,8 @@ def parse():
                     help="further transforms timed the same way and reported under 'paths' ('' for none)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-mode-seconds", type=float, default=3.0,
+                    help="seconds per additional oracle mode timed beside cpu_baseline (0: skip)")
     ap.add_argument("--ref-seconds", type=float, default=150.0,
                     help="CPU time budget of the whole --impl reference run")
     ap.add_argument("--no-cpu", action="store_true")
@@ -229,6 +231,49 @@ def cpu_oracle_rate(w, seconds):
     sample = (f"{n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block, "
               f"FP64 oracle FFT mode with autocorrelation removal, {cores} OpenMP threads, {dt:.1f} s")
     return units / dt, cores, sample
+
+
+def _grow(run, n_max, target_s):
+    """Smallest n (doubling from 1, at most n_max) whose run(n) takes about
+    target_s seconds; returns (n, seconds)."""
+    n = 1
+    while True:
+        t0 = time.perf_counter()
+        run(n)
+        dt = time.perf_counter() - t0
+        if dt >= 0.8 * target_s or n == n_max:
+            return n, dt
+        n = min(n_max, max(n + 1, int(n * min(8.0, target_s / max(dt, 1e-3)))))
+
+
+def cpu_oracle_modes(w, seconds):
+    """The oracle's other modes, each on a bounded sample of the station block
+    (about `seconds` each): the FFT mode on one thread, the direct separable DFT
+    on all cores, and the gridded FX image (visibilities of every antenna pair,
+    gridded with the kernels' cross-correlations, one transform; one thread).
+    Returns {mode: {"value", "unit", "cores", "sample"}}."""
+    oracle, arr, cores = _oracle_setup(w)
+    out = {}
+
+    def fft1(n_t):
+        oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=1, use_fft=True, n_threads=1)
+
+    def direct(n_t):
+        oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=min(cores, w.n_chan), use_fft=False,
+                     n_threads=cores)
+
+    def fx(n_t):
+        oracle.fx_gridded(arr, w.volts[:n_t], 0, include_autos=False)
+
+    for mode, fn, n_c, thr, what in [
+            ("fft_1thread", fft1, 1, 1, "FFT mode"),
+            ("direct_dft", direct, min(cores, w.n_chan), cores, "direct separable DFT"),
+            ("fx_gridded", fx, 1, 1, "gridded FX (visibilities, kernel cross-correlations, one DFT)")]:
+        n_t, dt = _grow(fn, w.n_time, seconds)
+        out[mode] = {"value": w.n_ant * n_c * n_t / dt, "unit": UNIT, "cores": thr,
+                     "sample": f"{n_c} channels x {n_t} samples x {w.n_ant} antennas, FP64 oracle {what}, "
+                               f"{thr} thread(s), {dt:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -555,6 +600,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if args.cpu_mode_seconds > 0:
+            cpu["modes"] = cpu_oracle_modes(w, args.cpu_mode_seconds)
 
     plan.close()
     if rank == 0:
