@@ -53,6 +53,8 @@ def parse():
                     help="further transforms timed the same way and reported under 'paths' ('' for none)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fma-iterations", type=int, default=100000,
+                    help="loop trips of the FMA-chain rate measurement (0: skip)")
     ap.add_argument("--cpu-mode-seconds", type=float, default=3.0,
                     help="seconds per additional oracle mode timed beside cpu_baseline (0: skip)")
     ap.add_argument("--ref-seconds", type=float, default=150.0,
@@ -595,6 +597,15 @@ def main():
     batch = None
     if args.batch_steps > 0:
         batch = time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind)
+
+    # the FP32 roofline's derived peak against a measured FMA-chain rate (after
+    # the timed regions, so it does not heat the GPU before them)
+    if args.fma_iterations > 0:
+        fma = epic.epic_debug_fma_rate(args.fma_iterations, stream)
+        for roof in [primary["roofline"]] + ([r["roofline"] for r in grid128.values()] if grid128 else []):
+            if roof.get("bound") == "alu":
+                roof["fma_chain_tflops"] = fma
+                roof["fma_chain_of_peak"] = fma / roof["peak"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

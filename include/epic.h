@@ -275,6 +275,14 @@ epic_status epic_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, void
 epic_status epic_debug_grid(epic_plan* plan, const uint8_t* d_volts, int n_time, int t, int c,
                             int p, float* d_grid, void* stream);
 
+/* Debug: the FP32 FMA rate the GPU sustains, measured by a kernel of
+ * independent dependent-FMA chains filling every SM (2 flop per FMA).  One
+ * warm-up launch, then one timed launch of `iterations` (1 .. 2^32) loop trips
+ * of 128 FMAs per thread, CUDA events on `stream`; *tflops receives TFLOP/s.
+ * Synchronous.  The denominator check of the FP32 path's roofline, whose peak
+ * is derived as SMs x 128 FP32 lanes x 2 flop x SM clock. */
+epic_status epic_debug_fma_rate(long long iterations, double* tflops, void* stream);
+
 /* Device time per kernel kind of a plan's launches, for benchmarks. */
 typedef struct {
   char kernel[32];      /* kernel kind, e.g. "fft_image", "reduce"              */

@@ -88,6 +88,7 @@ SIGNATURES = {
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "epic_debug_fma_rate": (_I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
     "epic_timing_enable": (_I, [_P, _I]),
     "epic_timing_read": (_I, [_P, ctypes.POINTER(epic_kernel_time), _I, ctypes.POINTER(_I)]),
 }
@@ -339,6 +340,14 @@ def epic_debug_unpack(d_in, n: int, d_out, stream=None) -> None:
 def epic_debug_grid(plan: Plan, d_volts, n_time: int, t: int, c: int, p: int, d_grid, stream=None) -> None:
     _check(load_library().epic_debug_grid(plan.handle, _ptr(d_volts), int(n_time), int(t), int(c), int(p),
                                           _ptr(d_grid), _stream(stream)), "epic_debug_grid")
+
+
+def epic_debug_fma_rate(iterations: int = 100000, stream=None) -> float:
+    """Measured FP32 FMA rate of the GPU in TFLOP/s (synchronous)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().epic_debug_fma_rate(int(iterations), ctypes.byref(out), _stream(stream)),
+           "epic_debug_fma_rate")
+    return out.value
 
 
 def epic_timing_enable(plan: Plan, enable: bool = True) -> None:

@@ -147,3 +147,15 @@ def test_two_plans_on_two_streams_match_sequential_calls():
     assert torch.equal(oa, ra) and torch.equal(ob, rb)
     pa.close()
     pb.close()
+
+
+def test_fma_chain_rate_is_near_the_derived_fp32_peak():
+    """The FP32 roofline's denominator (SMs x 128 lanes x 2 flop x the maximum
+    SM clock, 2070 MHz on GB300) checked against a measured FMA-chain rate."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = sms * 128 * 2 * 2070e6 / 1e12
+    rate = epic.epic_debug_fma_rate(20000)
+    assert 0.3 * derived < rate < 1.1 * derived, (rate, derived)
+    with pytest.raises(epic.EpicError):
+        epic.epic_debug_fma_rate(0)
