@@ -602,7 +602,9 @@ def main():
     # the timed regions, so it does not heat the GPU before them)
     if args.fma_iterations > 0:
         fma = epic.epic_debug_fma_rate(args.fma_iterations, stream)
-        for roof in [primary["roofline"]] + ([r["roofline"] for r in grid128.values()] if grid128 else []):
+        roofs = [primary["roofline"]] + [r["roofline"] for r in (grid128 or {}).values()
+                                          if isinstance(r, dict) and "roofline" in r]
+        for roof in roofs:
             if roof.get("bound") == "alu":
                 roof["fma_chain_tflops"] = fma
                 roof["fma_chain_of_peak"] = fma / roof["peak"]
