@@ -62,21 +62,31 @@ __device__ __forceinline__ void dft8(float2 (&x)[8]) {
 
 // Thread geometry of an N-point line transform: R1 threads per line, 8 points
 // per thread (element n1 + R1*n2 held by thread n1 as its n2-th value).
-// swz/scr are XOR layouts checked to be free of shared-memory bank conflicts
-// for every access pattern below.
+// swz is an XOR layout of the row buffer, scr a padded layout of the warp
+// scratch (slot (k2, n1) of line r, written by thread n1 and read by thread k2);
+// both were checked offline to be free of shared-memory bank conflicts for every
+// access pattern below.  scr is additive so that each thread's eight stores and
+// eight loads are one base address plus compile-time offsets.
 template <int N> struct Geo;
 template <> struct Geo<64> {
   static constexpr int R1 = 8, THREADS = 512, RPW = 4, SCR = 4 * 72;
   __device__ static int swz(int y) { return (9 * (y & 7)) & 15; }
-  __device__ static int scr(int r, int k2, int n1) { return r * 72 + k2 * 8 + (n1 ^ k2); }
+  __device__ static int scr(int r, int k2, int n1) { return r * 72 + 9 * k2 + n1; }
   // output index held as value s by thread q after a line transform
   __host__ __device__ static constexpr int kidx(int q, int s) { return q + 8 * s; }
+  // (kidx(n1, s) ^ sw) for the row buffer, written as two per-thread bases and
+  // a compile-time offset: n1 < 8 and sw < 16 leave the bits of 16 (s >> 1) alone
+  __device__ static int rowpos(int n1, int s, int sw) {
+    const int t = n1 ^ sw;
+    return ((s & 1) ? (t ^ 8) : t) + 16 * (s >> 1);
+  }
 };
 template <> struct Geo<32> {
   static constexpr int R1 = 4, THREADS = 128, RPW = 8, SCR = 8 * 36;
   __device__ static int swz(int y) { return (5 * (y & 7)) & 15; }
-  __device__ static int scr(int r, int k2, int n1) { return r * 36 + k2 * 4 + (n1 ^ ((k2 >> 1) & 3)); }
+  __device__ static int scr(int r, int k2, int n1) { return r * 36 + 4 * k2 + n1 + (k2 >> 1); }
   __host__ __device__ static constexpr int kidx(int q, int s) { return 2 * q + (s >> 2) + 8 * (s & 3); }
+  __device__ static int rowpos(int n1, int s, int sw) { return kidx(n1, s) ^ sw; }
 };
 
 // One N-point transform of a line held by R1 threads (Cooley-Tukey N = R1 x 8):
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
         fft_line<N>(v[p], tw, scr, r, n1);
         float2* Rrow = Rbuf + (size_t)p * NN + y * N;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) Rrow[G::kidx(n1, s) ^ sw] = v[p][s];
+        for (int s = 0; s < 8; ++s) Rrow[G::rowpos(n1, s, sw)] = v[p][s];
       }
     }
     __syncthreads();
@@ -699,7 +709,7 @@ __global__ void __launch_bounds__(512, 1)
         fft_line<N>(v[p], tw, scr, r, n1);
         float2* Rrow = Rbuf + (size_t)p * NN + y * N;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) Rrow[G::kidx(n1, s) ^ sw] = v[p][s];
+        for (int s = 0; s < 8; ++s) Rrow[G::rowpos(n1, s, sw)] = v[p][s];
       }
     }
     __syncthreads();
@@ -743,10 +753,10 @@ __global__ void __launch_bounds__(512, 1)
         float2 v[8];
         float2* Rrow = Rbuf + (size_t)p * NN + y * N;
 #pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rrow[(n1 + R1 * n2) ^ sw];
+        for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rrow[G::rowpos(n1, n2, sw)];
         fft_line<N>(v, tw, scr, r, n1);
 #pragma unroll
-        for (int s = 0; s < 8; ++s) Rrow[G::kidx(n1, s) ^ sw] = make_float2(v[s].x, -v[s].y);
+        for (int s = 0; s < 8; ++s) Rrow[G::rowpos(n1, s, sw)] = make_float2(v[s].x, -v[s].y);
       }
     }
     __syncthreads();
