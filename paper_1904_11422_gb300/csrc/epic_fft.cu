@@ -152,7 +152,9 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int e
 // reduction interleaves the four 64 x 64 partial images (pixel (j, i) of subset
 // q is pixel (2 j + beta, 2 i + alpha)).  `twiddle` then holds the 128-point
 // table, `C` the real channel count.
-template <int N, int P, bool Q = false>
+// KA: antennas per thread whose bytes are prefetched (1 when the array fits the
+// block, else enough for kMaxAnt), which keeps registers free for small arrays.
+template <int N, int P, bool Q = false, int KA = (kMaxAnt + Geo<N>::THREADS - 1) / Geo<N>::THREADS>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     fft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
                      const float2* __restrict__ twiddle, float* __restrict__ part, int* __restrict__ part_auto) {
   using G = Geo<N>;
   constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2;
-  constexpr int MAXK = (kMaxAnt + NT - 1) / NT;
+  constexpr int MAXK = KA;
   constexpr int NPL = (P == 2) ? 4 : 1;
 
   extern __shared__ __align__(16) unsigned char smem[];
@@ -374,9 +376,40 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 template <int N, int P>
 cudaError_t occupancy(int threads, size_t smem, int* per_sm) {
   cudaError_t e = allow_max_smem(fft_image_kernel<N, P>);
+  if (e == cudaSuccess) e = allow_max_smem(fft_image_kernel<N, P, false, 1>);
   if (e == cudaSuccess && N == 64) e = allow_max_smem(fft_image_kernel<64, P, true>);
+  if (e == cudaSuccess && N == 64) e = allow_max_smem(fft_image_kernel<64, P, true, 1>);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fft_image_kernel<N, P>, threads, smem);
+}
+
+// One imaging launch with the prefetch sized for the array.
+template <int N, int P, bool Q>
+cudaError_t launch_image(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, const float2* coef,
+                         float* part, int* part_auto, cudaStream_t s) {
+  if (p.A <= Geo<N>::THREADS)
+    fft_image_kernel<N, P, Q, 1><<<ws.ctas, p.threads, p.smem, s>>>(
+        d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+        p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
+  else
+    fft_image_kernel<N, P, Q><<<ws.ctas, p.threads, p.smem, s>>>(
+        d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
+        p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
+  return cudaGetLastError();
+}
+
+// Every N x N FP32 imaging launch not run on clusters: 32 x 32, 64 x 64, and
+// 128 x 128 grids as four folded 64 x 64 problems.
+cudaError_t launch_image_any(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, const float2* coef,
+                             float* part, int* part_auto, cudaStream_t s) {
+  if (p.N == 128)
+    return p.P == 2 ? launch_image<64, 2, true>(p, d_volts, T, ws, coef, part, part_auto, s)
+                    : launch_image<64, 1, true>(p, d_volts, T, ws, coef, part, part_auto, s);
+  if (p.N == 64)
+    return p.P == 2 ? launch_image<64, 2, false>(p, d_volts, T, ws, coef, part, part_auto, s)
+                    : launch_image<64, 1, false>(p, d_volts, T, ws, coef, part, part_auto, s);
+  return p.P == 2 ? launch_image<32, 2, false>(p, d_volts, T, ws, coef, part, part_auto, s)
+                  : launch_image<32, 1, false>(p, d_volts, T, ws, coef, part, part_auto, s);
 }
 
 size_t smem_for(const Plan& p, int ent_in_smem) {
@@ -440,58 +473,14 @@ cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
 }
 
 cudaError_t launch_fft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, cudaStream_t s) {
-  if (p.N == 128 && p.vq == 4) {  // four folded 64 x 64 problems per channel
-    if (p.P == 2)
-      fft_image_kernel<64, 2, true><<<ws.ctas, p.threads, p.smem, s>>>(
-          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, p.d_part, p.d_part_auto);
-    else
-      fft_image_kernel<64, 1, true><<<ws.ctas, p.threads, p.smem, s>>>(
-          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, p.d_part, p.d_part_auto);
-    return cudaGetLastError();
-  }
-  if (p.N == 128) return launch_fft128_image_ws(p, d_volts, T, ws, p.d_part, p.d_part_auto, s);
-  const int ent = p.ent_in_smem;
-#define EPIC_LAUNCH(NN_, PP_)                                                                                   \
-  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
-      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
-      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
-  if (p.N == 64) {
-    if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
-  } else {
-    if (p.P == 2) EPIC_LAUNCH(32, 2); else EPIC_LAUNCH(32, 1);
-  }
-#undef EPIC_LAUNCH
-  return cudaGetLastError();
+  if (p.N == 128 && p.vq == 1) return launch_fft128_image_ws(p, d_volts, T, ws, p.d_part, p.d_part_auto, s);
+  return launch_image_any(p, d_volts, T, ws, p.d_coef, p.d_part, p.d_part_auto, s);
 }
 
 cudaError_t launch_fft_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                                 int* part_auto, cudaStream_t s) {
-  if (p.N == 128 && p.vq == 4) {  // four folded 64 x 64 problems per channel
-    if (p.P == 2)
-      fft_image_kernel<64, 2, true><<<ws.ctas, p.threads, p.smem, s>>>(
-          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
-    else
-      fft_image_kernel<64, 1, true><<<ws.ctas, p.threads, p.smem, s>>>(
-          d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-          p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
-    return cudaGetLastError();
-  }
-  if (p.N == 128) return launch_fft128_image_ws(p, d_volts, T, ws, part, part_auto, s);
-  const int ent = p.ent_in_smem;
-#define EPIC_LAUNCH(NN_, PP_)                                                                                   \
-  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
-      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,          \
-      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, part, part_auto)
-  if (p.N == 64) {
-    if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
-  } else {
-    if (p.P == 2) EPIC_LAUNCH(32, 2); else EPIC_LAUNCH(32, 1);
-  }
-#undef EPIC_LAUNCH
-  return cudaGetLastError();
+  if (p.N == 128 && p.vq == 1) return launch_fft128_image_ws(p, d_volts, T, ws, part, part_auto, s);
+  return launch_image_any(p, d_volts, T, ws, p.d_coef, part, part_auto, s);
 }
 
 cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol, float* d_grid,
@@ -800,18 +789,7 @@ __global__ void __launch_bounds__(512, 1)
 
 cudaError_t launch_fft_image_coef(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, const float2* coef,
                                   cudaStream_t s) {
-  const int ent = p.ent_in_smem;
-#define EPIC_LAUNCH(NN_, PP_)                                                                                   \
-  fft_image_kernel<NN_, PP_><<<ws.ctas, p.threads, p.smem, s>>>(                                              \
-      d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,            \
-      p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_part, p.d_part_auto)
-  if (p.N == 64) {
-    if (p.P == 2) EPIC_LAUNCH(64, 2); else EPIC_LAUNCH(64, 1);
-  } else {
-    if (p.P == 2) EPIC_LAUNCH(32, 2); else EPIC_LAUNCH(32, 1);
-  }
-#undef EPIC_LAUNCH
-  return cudaGetLastError();
+  return launch_image_any(p, d_volts, T, ws, coef, p.d_part, p.d_part_auto, s);
 }
 
 namespace {
