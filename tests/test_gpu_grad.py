@@ -36,6 +36,8 @@ def _gpu_grad(w, gains, model):
 CASES = [
     dict(seed=1301, n_ant=12, n_pol=2, n_chan=2, grid_n=64, support=3, n_time=6),
     dict(seed=1302, n_ant=9, n_pol=1, n_chan=3, grid_n=64, support=5, n_time=5),
+    # more antennas than half the block: one thread per antenna in the degrid
+    dict(seed=1306, n_ant=300, n_pol=2, n_chan=1, grid_n=64, support=3, n_time=3),
 ]
 
 
