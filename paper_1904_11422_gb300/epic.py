@@ -146,7 +146,23 @@ def _ptr(x) -> int | None:
     raise TypeError(f"cannot pass {type(x)} as a pointer")
 
 
-def _dev_tensor(x, dtype_name: str, what: str):
+def _nbytes(x) -> int | None:
+    if hasattr(x, "element_size"):
+        return x.numel() * x.element_size()
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    return None  # a bare address: its extent is the caller's to guarantee
+
+
+def _check_size(x, nbytes: int | None, what: str) -> None:
+    """The kernels index a buffer by the plan's sizes; a smaller one would be read
+    or written out of bounds, so it is refused here."""
+    have = _nbytes(x)
+    if nbytes is not None and have is not None and have < nbytes:
+        raise ValueError(f"{what} holds {have} bytes; this call needs {nbytes}")
+
+
+def _dev_tensor(x, dtype_name: str, what: str, nbytes: int | None = None):
     if hasattr(x, "is_cuda"):
         if not x.is_cuda:
             raise ValueError(f"{what} must be a CUDA tensor")
@@ -154,6 +170,21 @@ def _dev_tensor(x, dtype_name: str, what: str):
             raise ValueError(f"{what} must be contiguous")
         if str(x.dtype) != f"torch.{dtype_name}":
             raise ValueError(f"{what} must be torch.{dtype_name}, got {x.dtype}")
+    _check_size(x, nbytes, what)
+    return _ptr(x)
+
+
+def _host_array(x, dtype_name: str, what: str, nbytes: int | None = None):
+    """A host buffer: a C-contiguous numpy array or CPU tensor of the given dtype."""
+    if hasattr(x, "is_cuda"):
+        if x.is_cuda:
+            raise ValueError(f"{what} must be a host (CPU) buffer")
+        if not x.is_contiguous() or str(x.dtype) != f"torch.{dtype_name}":
+            raise ValueError(f"{what} must be a contiguous torch.{dtype_name} tensor")
+    elif isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or x.dtype != np.dtype(dtype_name):
+            raise ValueError(f"{what} must be a C-contiguous {dtype_name} array")
+    _check_size(x, nbytes, what)
     return _ptr(x)
 
 
@@ -189,6 +220,22 @@ class Plan:
     def out_shape(self):
         i = self.info
         return (i["n_chan"], 4, i["grid_n"], i["grid_n"])
+
+    def volts_bytes(self, n_time: int) -> int:
+        """Bytes of a [n_time][n_chan][n_ant][n_pol] voltage block."""
+        i = self.info
+        return max(int(n_time), 0) * i["n_chan"] * i["n_ant"] * i["n_pol"]
+
+    @property
+    def out_bytes(self) -> int:
+        i = self.info
+        return 4 * i["n_chan"] * 4 * i["grid_n"] ** 2
+
+    @property
+    def gains_bytes(self) -> int:
+        """Bytes of [n_chan][n_ant][n_pol][2] float gains (and gradients)."""
+        i = self.info
+        return 4 * i["n_chan"] * i["n_ant"] * i["n_pol"] * 2
 
 
 def make_desc(ant_xy, chan_freq_hz, n_pol, grid_n, kernel_support, cell_lambda=0.5, kernel_sigma_cells=None,
@@ -242,8 +289,8 @@ def epic_plan_query(plan) -> dict:
 
 
 def epic_image(plan: Plan, d_volts, n_time: int, d_out, accumulate: int = 0, stream=None) -> None:
-    v = _dev_tensor(d_volts, "uint8", "d_volts") if d_volts is not None else None
-    o = _dev_tensor(d_out, "float32", "d_out")
+    v = _dev_tensor(d_volts, "uint8", "d_volts", plan.volts_bytes(n_time)) if d_volts is not None else None
+    o = _dev_tensor(d_out, "float32", "d_out", plan.out_bytes)
     _check(load_library().epic_image(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
            "epic_image")
 
@@ -251,8 +298,8 @@ def epic_image(plan: Plan, d_volts, n_time: int, d_out, accumulate: int = 0, str
 def epic_image_noalloc(plan: Plan, d_volts, n_time: int, d_out, accumulate: int = 0, stream=None) -> None:
     """epic_image without any device allocation: scratch from the library's static
     device array (EPIC_NOALLOC_SCRATCH_BYTES); calls that overlap on the GPU race."""
-    v = _dev_tensor(d_volts, "uint8", "d_volts") if d_volts is not None else None
-    o = _dev_tensor(d_out, "float32", "d_out")
+    v = _dev_tensor(d_volts, "uint8", "d_volts", plan.volts_bytes(n_time)) if d_volts is not None else None
+    o = _dev_tensor(d_out, "float32", "d_out", plan.out_bytes)
     _check(load_library().epic_image_noalloc(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
            "epic_image_noalloc")
 
@@ -261,23 +308,26 @@ EPIC_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def epic_image_host(plan: Plan, h_volts, n_time: int, h_out, accumulate: int = 0, stream=None) -> None:
-    _check(load_library().epic_image_host(plan.handle, _ptr(h_volts), int(n_time), _ptr(h_out),
-                                          int(accumulate), _stream(stream)), "epic_image_host")
+    v = _host_array(h_volts, "uint8", "h_volts", plan.volts_bytes(n_time)) if h_volts is not None else None
+    o = _host_array(h_out, "float32", "h_out", plan.out_bytes)
+    _check(load_library().epic_image_host(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
+           "epic_image_host")
 
 
 def epic_grad(plan: Plan, d_volts, n_time: int, d_gains, d_model, d_grad, d_loss, stream=None) -> None:
     """Loss and gain gradient of the image-plane calibration loss (see include/epic.h)."""
-    _check(load_library().epic_grad(plan.handle, _dev_tensor(d_volts, "uint8", "d_volts"), int(n_time),
-                                    _dev_tensor(d_gains, "float32", "d_gains"),
-                                    _dev_tensor(d_model, "float32", "d_model"),
-                                    _dev_tensor(d_grad, "float32", "d_grad"),
-                                    _dev_tensor(d_loss, "float32", "d_loss"), _stream(stream)), "epic_grad")
+    model_bytes = 4 * plan.info["n_chan"] * 2 * plan.info["grid_n"] ** 2
+    _check(load_library().epic_grad(plan.handle, _dev_tensor(d_volts, "uint8", "d_volts", plan.volts_bytes(n_time)),
+                                    int(n_time), _dev_tensor(d_gains, "float32", "d_gains", plan.gains_bytes),
+                                    _dev_tensor(d_model, "float32", "d_model", model_bytes),
+                                    _dev_tensor(d_grad, "float32", "d_grad", plan.gains_bytes),
+                                    _dev_tensor(d_loss, "float32", "d_loss", 4), _stream(stream)), "epic_grad")
 
 
 def epic_postprocess(plan: Plan, d_in, d_out, flags: int, beam_floor: float = 1e-3, stream=None) -> None:
     """Pseudo-Stokes planes and/or kernel-imprint division (see include/epic.h)."""
-    _check(load_library().epic_postprocess(plan.handle, _dev_tensor(d_in, "float32", "d_in"),
-                                           _dev_tensor(d_out, "float32", "d_out"), int(flags),
+    _check(load_library().epic_postprocess(plan.handle, _dev_tensor(d_in, "float32", "d_in", plan.out_bytes),
+                                           _dev_tensor(d_out, "float32", "d_out", plan.out_bytes), int(flags),
                                            float(beam_floor), _stream(stream)), "epic_postprocess")
 
 
@@ -305,9 +355,11 @@ class Batch:
 def epic_batch_create(plans, d_volts, n_time, d_out, tune: bool = False, stream=None) -> Batch:
     n = len(plans)
     hp = (_P * n)(*[p.handle for p in plans])
-    hv = (_P * n)(*[_dev_tensor(v, "uint8", "d_volts") for v in d_volts])
+    if not (len(d_volts) == len(n_time) == len(d_out) == n):
+        raise ValueError("plans, d_volts, n_time and d_out must have the same length")
+    hv = (_P * n)(*[_dev_tensor(v, "uint8", "d_volts", p.volts_bytes(t)) for p, v, t in zip(plans, d_volts, n_time)])
     ht = (_I * n)(*[int(t) for t in n_time])
-    ho = (_P * n)(*[_dev_tensor(o, "float32", "d_out") for o in d_out])
+    ho = (_P * n)(*[_dev_tensor(o, "float32", "d_out", p.out_bytes) for p, o in zip(plans, d_out)])
     chosen = (_I * n)()
     h = _P()
     _check(load_library().epic_batch_create(hp, n, hv, ht, ho, int(bool(tune)), chosen, _stream(stream),
@@ -333,11 +385,15 @@ def epic_status_string(status: int) -> str:
 
 
 def epic_debug_unpack(d_in, n: int, d_out, stream=None) -> None:
+    _check_size(d_in, max(int(n), 0), "d_in")
+    _check_size(d_out, 2 * max(int(n), 0), "d_out")
     _check(load_library().epic_debug_unpack(_ptr(d_in), int(n), _ptr(d_out), _stream(stream)),
            "epic_debug_unpack")
 
 
 def epic_debug_grid(plan: Plan, d_volts, n_time: int, t: int, c: int, p: int, d_grid, stream=None) -> None:
+    _check_size(d_volts, plan.volts_bytes(n_time), "d_volts")
+    _check_size(d_grid, 8 * plan.info["grid_n"] ** 2, "d_grid")
     _check(load_library().epic_debug_grid(plan.handle, _ptr(d_volts), int(n_time), int(t), int(c), int(p),
                                           _ptr(d_grid), _stream(stream)), "epic_debug_grid")
 

@@ -162,3 +162,25 @@ def test_validate_antenna_limits_small_grid_and_tensor_path(lib):
         ant = (rng.random((n_ant, 2)) - 0.5) * 20.0
         d, keep = epic.make_desc(ant, [50e6], 2, grid_n, 3, xform=xf)
         assert epic.epic_plan_validate(d) == code, (n_ant, grid_n, xf)
+
+
+def test_binding_size_and_layout_checks():
+    """Host-side argument checks of the binding (no GPU needed)."""
+    import torch
+    a = np.zeros(100, np.uint8)
+    epic._check_size(a, 100, "x")
+    epic._check_size(a.ctypes.data, 10**12, "x")  # a bare address is not checked
+    with pytest.raises(ValueError, match="holds 100 bytes"):
+        epic._check_size(a, 101, "x")
+    with pytest.raises(ValueError):
+        epic._check_size(torch.zeros(3, dtype=torch.float32), 13, "x")
+    h = np.zeros(4, np.float32)
+    assert epic._host_array(h, "float32", "h", 16) == h.ctypes.data
+    with pytest.raises(ValueError, match="holds 16 bytes"):
+        epic._host_array(h, "float32", "h", 17)
+    with pytest.raises(ValueError, match="C-contiguous float32"):
+        epic._host_array(np.zeros(4, np.float64), "float32", "h")
+    with pytest.raises(ValueError, match="C-contiguous uint8"):
+        epic._host_array(np.zeros((4, 4), np.uint8)[:, ::2], "uint8", "h")
+    with pytest.raises(ValueError, match="contiguous torch.float32"):
+        epic._host_array(torch.zeros(4, dtype=torch.float64), "float32", "h")

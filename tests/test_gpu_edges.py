@@ -106,8 +106,8 @@ def test_failed_staging_allocation_reports_oom_and_the_plan_keeps_working():
     plan = epic.plan_for(w)
     h_in = np.zeros(16, np.uint8)
     h_out = np.empty(plan.out_shape, np.float32)
-    with pytest.raises(epic.EpicError) as ei:
-        epic.epic_image_host(plan, h_in, 1 << 24, h_out, 0)
+    with pytest.raises(epic.EpicError) as ei:  # a bare address: only the library sees the size
+        epic.epic_image_host(plan, h_in.ctypes.data, 1 << 24, h_out, 0)
     assert ei.value.status == epic.EPIC_ERR_OOM
     dv = torch.from_numpy(w.volts).cuda()
     out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
@@ -159,3 +159,23 @@ def test_fma_chain_rate_is_near_the_derived_fp32_peak():
     assert 0.3 * derived < rate < 1.1 * derived, (rate, derived)
     with pytest.raises(epic.EpicError):
         epic.epic_debug_fma_rate(0)
+
+
+def test_undersized_buffers_are_refused_before_any_launch():
+    """The binding refuses buffers smaller than the plan's shapes (the kernels
+    would index past their ends); the plan keeps working."""
+    import torch
+    w = synth.random_small(2110, n_ant=8, n_pol=2, n_chan=3, grid_n=64, support=3, n_time=4)
+    plan = epic.plan_for(w)
+    dv = torch.from_numpy(w.volts).cuda()
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError, match="d_out"):
+        epic.epic_image(plan, dv, w.n_time, out[:2], 0)
+    with pytest.raises(ValueError, match="d_volts"):
+        epic.epic_image(plan, dv[:2].contiguous(), w.n_time, out, 0)
+    with pytest.raises(ValueError, match="h_out"):
+        epic.epic_image_host(plan, np.ascontiguousarray(w.volts), w.n_time, np.empty(10, np.float32), 0)
+    epic.epic_image(plan, dv, w.n_time, out, 0)
+    epic.epic_sync(plan)
+    assert_close(out.cpu().numpy(), oracle_image(w), 2)
+    plan.close()
