@@ -179,3 +179,22 @@ def test_undersized_buffers_are_refused_before_any_launch():
     epic.epic_sync(plan)
     assert_close(out.cpu().numpy(), oracle_image(w), 2)
     plan.close()
+
+
+@pytest.mark.parametrize("xf,grid_n,n_ant", [("fft_fp32", 64, 40), ("fft_fp32", 32, 20), ("dft_bf16x3", 64, 40),
+                                             ("fft_fp32", 128, 450), ("fft_fp32", 128, 30), ("dft_bf16x3", 128, 30)])
+def test_pinned_host_buffers_equal_device_call(xf, grid_n, n_ant):
+    """Page-locked host buffers through the host entry point give the
+    device-buffer call's result bit for bit, also on the 128 x 128 cluster (450
+    antennas x 5 x 5) and folded (30 antennas) kernels."""
+    import torch
+    w = synth.random_small(2111 + n_ant, n_ant=n_ant, n_pol=2, n_chan=3, grid_n=grid_n, support=5, n_time=17)
+    plan = epic.plan_for(w, epic.XFORMS[xf])
+    dev = gpu_image(w, xform=epic.XFORMS[xf], plan=plan)
+    h_in = torch.from_numpy(w.volts).pin_memory()
+    h_out = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+    epic.epic_image_host(plan, h_in, w.n_time, h_out, 0)
+    assert np.array_equal(h_out.numpy(), dev)
+    epic.epic_image_host(plan, h_in, w.n_time, h_out, 1)
+    assert np.allclose(h_out.numpy(), 2 * dev, rtol=1e-6, atol=1e-6 * np.abs(dev).max())
+    plan.close()
