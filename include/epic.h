@@ -114,11 +114,11 @@ typedef struct {
  * in some channel) or EPIC_ERR_UNSUPPORTED (a grid size or transform this
  * build does not implement: the FP32 FFT path takes N = 32, 64 or 128 with at
  * most 2048 antennas (a 128 x 128 grid runs on clusters of two CTAs when the
- * array has more than about 10 000 gather entries per channel and at most 1024
- * antennas, otherwise as four folded 64 x 64 problems); the tensor-core paths take N = 32, 64 or 128 (a 128 x 128 grid
- * is transformed as four 64 x 64 parity sub-problems, a 32 x 32 grid as one
- * zero-padded 64 x 64 problem), two polarisations and at most 1024
- * antennas). */
+ * array has more than 10 000 gather entries per channel, n_ant x S^2, and at
+ * most 1024 antennas, otherwise as four folded 64 x 64 problems); the
+ * tensor-core paths take N = 32, 64 or 128 (a 128 x 128 grid is transformed as
+ * four 64 x 64 parity sub-problems, a 32 x 32 grid as one zero-padded 64 x 64
+ * problem), two polarisations and at most 1024 antennas). */
 epic_status epic_plan_validate(const epic_plan_desc* desc);
 
 /* Creates a plan on the current CUDA device: validates desc, copies its
