@@ -1,10 +1,15 @@
-"""Channel sharding across ranks (one GPU per rank).
+"""Sharding across ranks (one GPU per rank).
 
 Channels are imaged independently (Sec. 5: each GPU of the deployment takes its
 own slice of the band), so a multi-GPU run splits the channels into contiguous,
 balanced ranges with no data-path collective.  Collectives appear only off the
 hot path: assembling the full image set on one rank, and the max-over-ranks
 timing of a benchmark.
+
+A block can instead be split over time: images with the autocorrelation term
+removed are additive over samples, so every rank images its own range of samples
+of all channels and one sum all-reduce of the [n_chan][4][N][N] accumulators per
+block gives the block's image (up to the order of the FP32 additions).
 """
 from __future__ import annotations
 
@@ -16,6 +21,19 @@ def channel_shard(n_chan: int, rank: int, world: int) -> tuple[int, int]:
     base, extra = divmod(n_chan, world)
     lo = rank * base + min(rank, extra)
     return lo, lo + base + (1 if rank < extra else 0)
+
+
+def time_shard(n_time: int, rank: int, world: int) -> tuple[int, int]:
+    """[t_lo, t_hi) of rank's samples of a block: contiguous, sizes differing by at most 1."""
+    return channel_shard(n_time, rank, world)
+
+
+def sum_images(local, group=None):
+    """The sum over ranks of each rank's image accumulators (in place; every rank
+    receives the block's image).  The one exchange of a time-split block."""
+    import torch.distributed as dist
+    dist.all_reduce(local, op=dist.ReduceOp.SUM, group=group)
+    return local
 
 
 def gather_channels(local, n_chan: int, group=None):

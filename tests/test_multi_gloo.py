@@ -1,5 +1,6 @@
 """Multi-rank host logic on CPU (gloo, world size 2): channel shards tile the
-band, gathered per-rank images equal the whole, and timings reduce to the max."""
+band, gathered per-rank images equal the whole, timings reduce to the max, and a
+block split over time sums to the whole image."""
 import os
 import socket
 
@@ -64,3 +65,35 @@ def test_sharded_images_equal_the_whole(tmp_path, oracle_lib):
     full = np.load(tmp_path / "full.npy")
     assert np.array_equal(full, whole)  # channels are independent: bit-identical
     assert np.load(tmp_path / "slowest.npy")[0] == 1.5 + world - 1
+
+
+def _time_worker(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    w = synth.random_small(78, n_ant=6, n_pol=2, n_chan=3, grid_n=16, support=3, n_time=9)
+    arr = oracle.OracleArray(w.ant_xy, w.freq_hz, 2, w.grid_n, w.support, w.cell_lambda, w.sigma_cells,
+                             gains=w.gains, delays=w.delays_s)
+    lo, hi = shard.time_shard(w.n_time, rank, world)
+    local = torch.from_numpy(oracle.image(arr, w.volts[lo:hi], subtract=True, n_threads=1))
+    total = shard.sum_images(local)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "total.npy"), total.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_time_split_block_sums_to_the_whole(tmp_path, oracle_lib):
+    """Ranks image disjoint sample ranges of every channel (autocorrelations removed
+    per rank); one sum all-reduce gives the whole block's image."""
+    world = 2
+    mp.spawn(_time_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    import oracle
+    w = synth.random_small(78, n_ant=6, n_pol=2, n_chan=3, grid_n=16, support=3, n_time=9)
+    arr = oracle.OracleArray(w.ant_xy, w.freq_hz, 2, w.grid_n, w.support, w.cell_lambda, w.sigma_cells,
+                             gains=w.gains, delays=w.delays_s)
+    whole = oracle.image(arr, w.volts, subtract=True, n_threads=1)
+    total = np.load(tmp_path / "total.npy")
+    assert np.abs(total - whole).max() <= 1e-12 * np.abs(whole).max()
+    assert [shard.time_shard(9, r, 2) for r in range(2)] == [(0, 5), (5, 9)]
