@@ -160,6 +160,20 @@ epic_status epic_image(epic_plan* plan, const uint8_t* d_volts, int n_time, floa
 epic_status epic_image_host(epic_plan* plan, const uint8_t* h_volts, int n_time, float* h_out,
                             int accumulate, void* stream);
 
+/* Streaming form of epic_image_host for page-locked (pinned) host buffers:
+ * enqueues the call and returns.  The input is copied to one of two plan-owned
+ * device slots on a plan-owned copy stream, imaged on `stream` once it has
+ * landed, and the [n_chan][4][N][N] result is copied to h_out on a second
+ * plan-owned copy stream; consecutive calls alternate slots, so the input copy
+ * of one call overlaps the imaging of the previous one.  h_volts must stay
+ * unchanged and h_out untouched until epic_sync(plan, stream) returns, which
+ * waits for every enqueued call and reports device errors.  Calls on one plan
+ * must use one stream (as for epic_image).  Images equal epic_image's bit for
+ * bit.  Returns EPIC_ERR_INVALID_ARG if h_volts (when n_time > 0) or h_out is
+ * not page-locked host memory. */
+epic_status epic_image_host_async(epic_plan* plan, const uint8_t* h_volts, int n_time, float* h_out,
+                                  int accumulate, void* stream);
+
 /* Size of the static device array that epic_image_noalloc takes its scratch
  * space from (32 MiB, held on every GPU that loads the library until exit). */
 #define EPIC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -90,6 +90,7 @@ void free_plan(Plan& p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   epic::free_gather_tables(p.gt);
+  epic::free_host_pipe(p);
 }
 
 
@@ -389,7 +390,9 @@ epic_status epic_plan_query(const epic_plan* h, epic_plan_info* info) {
   info->n_ant = p.A; info->n_pol = p.P; info->n_chan = p.C; info->grid_n = p.N;
   info->kernel_support = p.S; info->xform = p.xform; info->subtract_autos = p.subtract;
   info->device = p.device; info->ctas = p.ctas; info->threads_per_cta = p.threads;
-  info->device_bytes = p.device_bytes + p.stage_in_bytes + (p.d_stage_out ? sizeof(float) * 4 * p.C * p.N * p.N : 0);
+  const size_t out_bytes = sizeof(float) * 4 * p.C * p.N * p.N;
+  info->device_bytes = p.device_bytes + p.stage_in_bytes + (p.d_stage_out ? out_bytes : 0) + 2 * p.pipe.in_bytes +
+                       (p.pipe.d_out[0] ? 2 * out_bytes : 0);
   info->workspace_bytes = p.workspace_bytes;
   // integer self powers stay exact in int32 per CTA and the unit index in int64
   info->max_time = (1LL << 24);
@@ -462,6 +465,7 @@ epic_status epic_image_host(epic_plan* h, const uint8_t* h_volts, int n_time, fl
 epic_status epic_sync(epic_plan* h, void* stream) {
   if (!h) return EPIC_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && h->p.pipe.d2h) e = cudaStreamSynchronize(h->p.pipe.d2h);  // epic_image_host_async results
   if (e != cudaSuccess) return from_cuda(e);
   int status = 0;
   e = cudaMemcpy(&status, h->p.d_status, sizeof(int), cudaMemcpyDeviceToHost);

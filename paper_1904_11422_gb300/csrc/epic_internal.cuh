@@ -118,6 +118,18 @@ struct Plan {
   uint8_t* d_stage_in = nullptr;
   size_t stage_in_bytes = 0;
   float* d_stage_out = nullptr;
+
+  // epic_image_host_async: two staging slots used alternately, a stream for the
+  // input copies and one for the result copies, and per slot the events that
+  // order each buffer's reuse (input copied, imaged, result copied back)
+  struct HostPipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t copied[2] = {}, computed[2] = {}, returned[2] = {};
+    uint8_t* d_in[2] = {};
+    size_t in_bytes = 0;  // capacity of each input slot
+    float* d_out[2] = {};
+    int slot = 0;
+  } pipe;
 };
 
 // ---- launchers (each returns cudaGetLastError() of its launch) -------------
@@ -130,6 +142,8 @@ cudaError_t launch_postprocess(const Plan& p, const float* d_in, float* d_out, i
 // Builds p.gt from the per-cell table (two launches, synchronous).
 cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, size_t* bytes);
 void free_gather_tables(GatherTables& g);
+// Waits for and releases the streams, events and buffers of epic_image_host_async.
+void free_host_pipe(Plan& p);
 
 // FP32 FFT path: the fused unpack + calibrate + grid + FFT + products kernel.
 // Sets p.threads, p.smem, p.ent_in_smem and returns the resident CTAs per SM.

@@ -89,6 +89,7 @@ SIGNATURES = {
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "epic_debug_fma_rate": (_I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
+    "epic_image_host_async": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_timing_enable": (_I, [_P, _I]),
     "epic_timing_read": (_I, [_P, ctypes.POINTER(epic_kernel_time), _I, ctypes.POINTER(_I)]),
 }
@@ -312,6 +313,15 @@ def epic_image_host(plan: Plan, h_volts, n_time: int, h_out, accumulate: int = 0
     o = _host_array(h_out, "float32", "h_out", plan.out_bytes)
     _check(load_library().epic_image_host(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
            "epic_image_host")
+
+
+def epic_image_host_async(plan: Plan, h_volts, n_time: int, h_out, accumulate: int = 0, stream=None) -> None:
+    """Enqueues imaging from pinned host buffers (see include/epic.h); the result is
+    in h_out once epic_sync(plan, stream) returns."""
+    v = _host_array(h_volts, "uint8", "h_volts", plan.volts_bytes(n_time)) if h_volts is not None else None
+    o = _host_array(h_out, "float32", "h_out", plan.out_bytes)
+    _check(load_library().epic_image_host_async(plan.handle, v, int(n_time), o, int(accumulate), _stream(stream)),
+           "epic_image_host_async")
 
 
 def epic_grad(plan: Plan, d_volts, n_time: int, d_gains, d_model, d_grad, d_loss, stream=None) -> None:

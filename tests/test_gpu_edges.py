@@ -198,3 +198,61 @@ def test_pinned_host_buffers_equal_device_call(xf, grid_n, n_ant):
     epic.epic_image_host(plan, h_in, w.n_time, h_out, 1)
     assert np.allclose(h_out.numpy(), 2 * dev, rtol=1e-6, atol=1e-6 * np.abs(dev).max())
     plan.close()
+
+
+def test_async_host_calls_in_flight_equal_device_calls():
+    """Five pipelined calls from pinned buffers over three different blocks, then
+    one epic_sync: every result equals its device-buffer call bit for bit."""
+    import torch
+    w = synth.random_small(2120, n_ant=30, n_pol=2, n_chan=4, grid_n=64, support=5, n_time=23)
+    plan = epic.plan_for(w)
+    rng = np.random.default_rng(5)
+    blocks = [w.volts, rng.integers(0, 256, w.volts.shape, dtype=np.uint8), w.volts[::-1].copy()]
+    want = [gpu_image(w, plan=plan, volts=b) for b in blocks]
+    h_in = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in blocks]
+    outs = [torch.full(plan.out_shape, np.nan, dtype=torch.float32).pin_memory() for _ in range(5)]
+    order = [0, 1, 2, 1, 0]
+    for i, b in enumerate(order):
+        epic.epic_image_host_async(plan, h_in[b], w.n_time, outs[i], 0)
+    epic.epic_sync(plan)
+    for i, b in enumerate(order):
+        assert np.array_equal(outs[i].numpy(), want[b]), i
+    plan.close()
+
+
+def test_async_host_accumulation_chain_and_mixed_calls():
+    """Accumulating pipelined calls into one pinned buffer sees each previous
+    result; synchronous host calls and device calls interleave on the same plan."""
+    import torch
+    w = synth.random_small(2121, n_ant=12, n_pol=2, n_chan=3, grid_n=32, support=3, n_time=9)
+    plan = epic.plan_for(w)
+    dev = gpu_image(w, plan=plan)
+    h_in = torch.from_numpy(w.volts).pin_memory()
+    acc = torch.zeros(plan.out_shape, dtype=torch.float32).pin_memory()
+    for i in range(4):
+        epic.epic_image_host_async(plan, h_in, w.n_time, acc, 1)
+    epic.epic_sync(plan)
+    assert np.allclose(acc.numpy(), 4 * dev, rtol=1e-5, atol=1e-5 * np.abs(dev).max())
+    h_out = np.empty(plan.out_shape, np.float32)
+    epic.epic_image_host(plan, np.ascontiguousarray(w.volts), w.n_time, h_out, 0)
+    assert np.array_equal(h_out, dev)
+    one = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+    epic.epic_image_host_async(plan, h_in, w.n_time, one, 0)
+    epic.epic_sync(plan)
+    assert np.array_equal(one.numpy(), dev)
+    plan.close()
+
+
+def test_async_host_call_rejects_pageable_buffers():
+    import torch
+    w = synth.random_small(2122, n_ant=6, n_pol=2, n_chan=2, grid_n=32, support=3, n_time=3)
+    plan = epic.plan_for(w)
+    pinned_out = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_image_host_async(plan, np.ascontiguousarray(w.volts), w.n_time, pinned_out, 0)
+    assert ei.value.status == epic.EPIC_ERR_INVALID_ARG
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_image_host_async(plan, torch.from_numpy(w.volts).pin_memory(), w.n_time,
+                                   np.empty(plan.out_shape, np.float32), 0)
+    assert ei.value.status == epic.EPIC_ERR_INVALID_ARG
+    plan.close()
