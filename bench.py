@@ -418,6 +418,17 @@ def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
                              "frac": fl / (ms / 1e3) / 1e12 / peak, "flops_per_launch": fl,
                              "basis": f"issued BF16 x3 flops of arrays A, B and C over the whole graph time; "
                                       f"peak: measured dense BF16 cuBLAS burst ({pk_kind})"}
+        else:
+            # algorithmic FP32 flops of the batch (each grid's transform counted as
+            # one N x N FFT, as in the single-plan rooflines) over the graph time
+            fl = sum(w.n_chan * w.n_time * fp32_flops_per_tc(w.n_ant, w.n_pol, w.grid_n, w.support) for w in ws)
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            r["roofline"] = {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": fl / (ms / 1e3) / 1e12 / peak, "flops_per_launch": fl,
+                             "basis": f"algorithmic FP32 flops of arrays A, B and C over the whole graph time; "
+                                      f"peak derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
+                                      f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind})"}
         res[name] = r
         b.close()
         for p in plans:
