@@ -154,8 +154,10 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int e
 // table, `C` the real channel count.
 // KA: antennas per thread whose bytes are prefetched (1 when the array fits the
 // block, else enough for kMaxAnt), which keeps registers free for small arrays.
+// At N = 32 (128-thread blocks) four blocks share an SM: 16 warps hide latency
+// that the two blocks of an unbounded register allocation could not.
 template <int N, int P, bool Q = false, int KA = (kMaxAnt + Geo<N>::THREADS - 1) / Geo<N>::THREADS>
-__global__ void __launch_bounds__(Geo<N>::THREADS, 1)
+__global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     fft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
                      const int* __restrict__ g_off, const uint16_t* __restrict__ g_ent_a,
