@@ -323,17 +323,17 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   int clusters = 0;  // N = 128: the imaging launch counts clusters of two CTAs
   if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128 && fft128_fold(p.A, p.S)) {
     p.vq = 4;
-    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft64Q, 512, 0, &gt_bytes));
+    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft64Q, 512, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(epic::fft_image_config(p, &per_sm));
   } else if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128) {
-    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft128, 1024, 0, &gt_bytes));
+    EPIC_TRY(epic::build_gather_tables(p, epic::kLayoutFft128, 1024, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(epic::fft128_config(p, &clusters));
     if (clusters < 1) return fail(cudaErrorInvalidConfiguration);
   } else if (p.xform == EPIC_XFORM_FFT_FP32) {
     EPIC_TRY(epic::build_gather_tables(p, p.N == 64 ? epic::kLayoutFft64 : epic::kLayoutFft32,
-                                       p.N == 64 ? 512 : 128, 0, &gt_bytes));
+                                       p.N == 64 ? 512 : 128, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(epic::fft_image_config(p, &per_sm));
   } else {
@@ -342,7 +342,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
     p.vq = p.N == 128 ? 4 : 1;
     p.dec = p.N == 32 ? 2 : 1;
     const int layout = p.N == 128 ? epic::kLayoutPairQ : p.N == 32 ? epic::kLayoutPairD : epic::kLayoutPair64;
-    EPIC_TRY(epic::build_gather_tables(p, layout, 512, 0, &gt_bytes));
+    EPIC_TRY(epic::build_gather_tables(p, layout, 512, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(alloc(&p.d_fmat, (size_t)4 * 128 * 128 / 2, &total));
     EPIC_TRY(epic::launch_dft_tables(p, 0));

@@ -19,7 +19,6 @@
 //   kFft32: y = t / 4, x = t % 4 + 4 s   (N = 32)
 //   kFft128: y = t / 8, x = t % 8 + 8 s, s < 16 (N = 128; 1024 tasks, the
 //            two CTAs of a cluster: tasks 512 r + i belong to CTA r)
-//   kChunk64: y = t / 8, x = 8 (t % 8) + s (eight consecutive cells)
 //   kPair64: four load-balanced cell pairs per thread (tensor path, see deal_pairs)
 //   kPairQ: the same over the 64 x 64 field H_q that the tensor path transforms
 //           for output-parity subset q of a 128 x 128 grid: H_q(y, x) sums the
@@ -32,23 +31,17 @@
 //   kPairD: the same over a 64 x 64 field holding a 32 x 32 grid in its cells
 //           y, x < 32 (zero elsewhere): the tensor path's transform of 32 x 32
 //           grids, whose even output pixels are the 32-point transform.
-// With sorting on, tasks are ordered by their number of entries (stable), so
-// warps get cells of similar load; thread i of a channel then works on task
-// task[i].
 #include "epic_internal.cuh"
 
 namespace epic {
 
 namespace {
 
+// Cell (y, x) of slot s of thread `task` in the FFT row layouts (kFft64, kFft64Q,
+// kFft128: eight threads per row; kFft32: four).
 __device__ __forceinline__ int2 cell_of(int layout, int task, int s) {
-  switch (layout) {
-    case kLayoutFft64:
-    case kLayoutFft64Q:
-    case kLayoutFft128: return make_int2(task >> 3, (task & 7) + 8 * s);
-    case kLayoutFft32: return make_int2(task >> 2, (task & 3) + 4 * s);
-    default: return make_int2(task >> 3, 8 * (task & 7) + s);
-  }
+  if (layout == kLayoutFft32) return make_int2(task >> 2, (task & 3) + 4 * s);
+  return make_int2(task >> 3, (task & 7) + 8 * s);
 }
 
 // Grid cell of field cell (y, x), or -1 where the field is zero (kLayoutPairD
@@ -98,7 +91,7 @@ __device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int* load
 
 // One CTA of nt threads per channel.  fill = 0: only the padded entry count of
 // the channel (tot[c]); fill = 1: also every table.
-__global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int fill, const int* __restrict__ csr_ptr,
+__global__ void gather_tables_kernel(int layout, int N, int nnz, int fill, const int* __restrict__ csr_ptr,
                                      const int2* __restrict__ csr_ent, const int* __restrict__ chan_off,
                                      int* __restrict__ tot, int* __restrict__ cnt_out, int* __restrict__ base_out,
                                      uint16_t* __restrict__ task_out, uint16_t* __restrict__ ent_a,
@@ -109,9 +102,9 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
   int* kws = sh;                 // [warps * ns]
   int* bws = kws + warps * ns;   // [warps * ns]
   const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
-  int* keys = bws + warps * ns;  // [nt], or [2048] for pairs
-  int* perm = keys + (pairs ? 2048 : nt);     // [nt], or [2048]
-  int* pair_of = perm + (pairs ? 2048 : nt);  // [4 nt] (pairs only)
+  int* keys = bws + warps * ns;  // [2048] (pairs only)
+  int* perm = keys + 2048;       // [2048] (pairs only)
+  int* pair_of = perm + 2048;    // [4 nt] (pairs only)
   // table set (channel, or virtual channel 4 c + q) and the grid channel it reads
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int cg = layout_folded(layout) ? c >> 2 : c;
@@ -127,20 +120,6 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
       cells[s] = make_int2(q >> 5, 2 * (q & 31) + (s & 1));
     }
   } else {
-    int key = 0;
-    for (int s = 0; s < ns; ++s) {
-      const int2 yx = cell_of(layout, tid, s);
-      key += field_count(layout, ptr, N, yx.x, yx.y);
-    }
-    if (sorted) {
-      keys[tid] = key;
-      __syncthreads();
-      int rank = 0;
-      for (int j = 0; j < nt; ++j) rank += (keys[j] < key) || (keys[j] == key && j < tid);
-      perm[rank] = tid;
-      __syncthreads();
-      task = perm[tid];
-    }
     for (int s = 0; s < ns; ++s) cells[s] = cell_of(layout, task, s);
   }
   int cnt[16], beg[16];
@@ -219,22 +198,21 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int sorted, int
 
 }  // namespace
 
-cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, size_t* total_bytes) {
+cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* total_bytes) {
   GatherTables& g = p.gt;
   g.layout = layout;
   g.threads = threads;
-  g.sorted = sorted;
   const int warps = threads / 32;
   const int ns = layout == kLayoutFft128 ? 16 : 8;
   const int nnz = p.A * p.S * p.S;
   const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
   const int nsets = layout_folded(layout) ? 4 * p.C : p.C;  // table sets (virtual channels)
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
-                                     (pairs ? 2 * 2048 + 4 * (size_t)threads : 2 * (size_t)threads));
+                                     (pairs ? 2 * 2048 + 4 * (size_t)threads : 0));
   int* d_tot = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * nsets);
   if (e != cudaSuccess) return e;
-  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, sorted, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
                                                nullptr, nullptr, nullptr, nullptr, nullptr);
   e = cudaGetLastError();
   std::vector<int> tot(nsets);
@@ -265,7 +243,7 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, si
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_w), sizeof(float) * total)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (nsets + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
-  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, sorted, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
                                                nullptr, g.d_cnt, g.d_base, g.d_task, g.d_ent_a, g.d_ent_w);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

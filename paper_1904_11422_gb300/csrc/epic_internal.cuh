@@ -39,13 +39,13 @@ struct WorkSplit {
 };
 
 // Gather tables of a gridder (see epic_gather.cu).
-enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutChunk64 = 2, kLayoutPair64 = 3, kLayoutFft128 = 4,
+enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutPair64 = 3, kLayoutFft128 = 4,
              kLayoutPairQ = 5, kLayoutPairD = 6, kLayoutFft64Q = 7 };
 // Layouts whose table set 4 c + q gathers the 128 x 128 grid of channel c folded
 // into the 64 x 64 field H_q of output-parity subset q.
 __host__ __device__ inline bool layout_folded(int layout) { return layout == kLayoutPairQ || layout == kLayoutFft64Q; }
 struct GatherTables {
-  int layout = 0, threads = 0, sorted = 0;
+  int layout = 0, threads = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel
   int* d_cnt = nullptr;          // [C][warps][slots] trip count of (warp, slot); 8 slots, 16 at N = 128
   int* d_base = nullptr;         // [C][warps][slots] first entry of (warp, slot) within the channel
@@ -140,7 +140,7 @@ cudaError_t launch_beam(Plan& p, cudaStream_t s);
 cudaError_t launch_postprocess(const Plan& p, const float* d_in, float* d_out, int flags, float floor,
                                cudaStream_t s);
 // Builds p.gt from the per-cell table (two launches, synchronous).
-cudaError_t build_gather_tables(Plan& p, int layout, int threads, int sorted, size_t* bytes);
+cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* bytes);
 void free_gather_tables(GatherTables& g);
 // Waits for and releases the streams, events and buffers of epic_image_host_async.
 void free_host_pipe(Plan& p);
