@@ -289,6 +289,14 @@ epic_status epic_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, void
 epic_status epic_debug_grid(epic_plan* plan, const uint8_t* d_volts, int n_time, int t, int c,
                             int p, float* d_grid, void* stream);
 
+/* Debug: the pre-square image Y = FT{W * E'} (Eq. (5) before squaring) of sample
+ * t, channel c, polarisation p, as d_y [N][N][2] float (row m, column l, re/im;
+ * pixel N/2 is the zero frequency), computed with the imaging kernel's own
+ * line transforms and shared-memory layouts on the field that epic_debug_grid
+ * returns.  FP32 FFT plans with N = 32 or 64 (else EPIC_ERR_UNSUPPORTED). */
+epic_status epic_debug_transform(epic_plan* plan, const uint8_t* d_volts, int n_time, int t, int c, int p,
+                                 float* d_y, void* stream);
+
 /* Debug: the FP32 FMA rate the GPU sustains, measured by a kernel of
  * independent dependent-FMA chains filling every SM (2 flop per FMA).  One
  * warm-up launch, then one timed launch of `iterations` (1 .. 2^32) loop trips

@@ -519,6 +519,16 @@ epic_status epic_debug_grid(epic_plan* h, const uint8_t* d_volts, int n_time, in
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
+epic_status epic_debug_transform(epic_plan* h, const uint8_t* d_volts, int n_time, int t, int c, int p, float* d_y,
+                                 void* stream) {
+  if (!h || !d_volts || !d_y || n_time < 1 || t < 0 || t >= n_time || c < 0 || c >= h->p.C || p < 0 ||
+      p >= h->p.P)
+    return EPIC_ERR_INVALID_ARG;
+  if (h->p.xform != EPIC_XFORM_FFT_FP32 || (h->p.N != 32 && h->p.N != 64)) return EPIC_ERR_UNSUPPORTED;
+  return from_cuda(epic::launch_debug_transform(h->p, d_volts, n_time, t, c, p, d_y,
+                                                reinterpret_cast<cudaStream_t>(stream)));
+}
+
 epic_status epic_timing_enable(epic_plan* h, int enable) {
   if (!h || (enable != 0 && enable != 1)) return EPIC_ERR_INVALID_ARG;
   Plan& p = h->p;

@@ -461,7 +461,99 @@ __global__ void debug_grid_kernel(const uint8_t* __restrict__ volts, int T, int 
   }
 }
 
+// The transform step alone, for the debug entry point: the gridded field of one
+// (t, c, pol) (the CSR order and FP32 fused multiply-adds of the gather), then
+// the imaging kernel's own row pass and column pass (the same line transforms,
+// twiddles and shared-memory layouts), written out with the pixel shift of
+// reading R4: out[row m][column l][re, im].  One CTA of the imaging block size.
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS)
+    debug_transform_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, int P, int t, int c, int pol,
+                           const float2* __restrict__ coef, const int* __restrict__ csr_ptr,
+                           const int2* __restrict__ csr_ent, int nnz, const float2* __restrict__ twiddle,
+                           float* __restrict__ out) {
+  using G = Geo<N>;
+  constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* Rbuf = reinterpret_cast<float2*>(smem);  // [N][N], rows XOR-swizzled as in the imaging kernel
+  float2* scr_all = Rbuf + NN;                     // [warps][SCR]
+  float2* E = scr_all + (NT / 32) * G::SCR;        // [A] calibrated fields of polarisation pol
+  const int tid = threadIdx.x, line = tid / R1, n1 = tid % R1, r = line % G::RPW;
+  float2* scr = scr_all + (tid >> 5) * G::SCR;
+
+  const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
+  for (int a = tid; a < A; a += NT) {
+    const unsigned b = base[a * P + pol];
+    const int re = nib_hi(b), im = nib_lo(b);
+    const float2 k = coef[((size_t)c * A + a) * P + pol];
+    E[a] = make_float2(k.x * re - k.y * im, k.x * im + k.y * re);
+  }
+  __syncthreads();
+  const int* ptr = csr_ptr + (size_t)c * (NN + 1);
+  const int2* ent = csr_ent + (size_t)c * nnz;
+  for (int cell = tid; cell < NN; cell += NT) {
+    float2 g = make_float2(0.f, 0.f);
+    for (int e = ptr[cell]; e < ptr[cell + 1]; ++e) {
+      const int2 en = ent[e];
+      const float w = __int_as_float(en.y);
+      g.x = fmaf(w, E[en.x].x, g.x);
+      g.y = fmaf(w, E[en.x].y, g.y);
+    }
+    const int y = cell / N, x = cell % N;
+    Rbuf[y * N + (x ^ G::swz(y))] = g;
+  }
+  __syncthreads();
+
+  float2 tw[8];
+  tw[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[(n1 * k2) & (N - 1)];
+  {  // row pass: thread (row y, n1) holds cells (y, n1 + R1 n2)
+    const int y = line, sw = G::swz(y);
+    float2 v[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rbuf[y * N + ((n1 + R1 * n2) ^ sw)];
+    fft_line<N>(v, tw, scr, r, n1);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) Rbuf[y * N + G::rowpos(n1, s, sw)] = v[s];
+  }
+  __syncthreads();
+  {  // column pass: thread (column k, n1) ends with rows kidx(n1, s) of column k
+    const int k = line;
+    float2 v[8];
+#pragma unroll
+    for (int m2 = 0; m2 < 8; ++m2) {
+      const int y = n1 + R1 * m2;
+      v[m2] = Rbuf[y * N + (k ^ G::swz(y))];
+    }
+    fft_line<N>(v, tw, scr, r, n1);
+    const int col = (k + HALF) & (N - 1);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int row = (G::kidx(n1, s) + HALF) & (N - 1);
+      out[2 * (row * N + col)] = v[s].x;
+      out[2 * (row * N + col) + 1] = v[s].y;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_debug_transform(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol, float* d_y,
+                                   cudaStream_t s) {
+  const int nnz = p.A * p.S * p.S;
+  auto run = [&](auto kernel, int threads, int n) -> cudaError_t {
+    const size_t scr = (size_t)(threads / 32) * (n == 64 ? Geo<64>::SCR : Geo<32>::SCR);
+    const size_t smem = sizeof(float2) * ((size_t)n * n + scr + p.A);
+    cudaError_t e = allow_max_smem(kernel);
+    if (e != cudaSuccess) return e;
+    kernel<<<1, threads, smem, s>>>(d_volts, T, p.C, p.A, p.P, t, c, pol, p.d_coef, p.d_csr_ptr, p.d_csr_ent, nnz,
+                                    p.d_twiddle, d_y);
+    return cudaGetLastError();
+  };
+  return p.N == 64 ? run(debug_transform_kernel<64>, Geo<64>::THREADS, 64)
+                   : run(debug_transform_kernel<32>, Geo<32>::THREADS, 32);
+}
 
 cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
   p.ent_in_smem = ent_fits(p) ? 1 : 0;

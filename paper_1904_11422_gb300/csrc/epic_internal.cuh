@@ -199,6 +199,10 @@ cudaError_t launch_reduce_ws(const Plan& p, int T, const WorkSplit& ws, const fl
 cudaError_t launch_debug_unpack(const uint8_t* d_in, size_t n, int8_t* d_out, cudaStream_t s);
 cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol,
                               float* d_grid, cudaStream_t s);
+// The pre-square image Y of one (t, c, pol) through the imaging kernel's line
+// transforms (FP32 plans, N = 32 or 64); d_y [N][N][2].
+cudaError_t launch_debug_transform(Plan& p, const uint8_t* d_volts, int T, int t, int c, int pol, float* d_y,
+                                   cudaStream_t s);
 
 // ---- small device helpers shared by the kernels ----------------------------
 // Sec. 3.2: one byte = 4-bit real (high nibble) + 4-bit imaginary (low nibble),

@@ -88,6 +88,7 @@ SIGNATURES = {
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "epic_debug_transform": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "epic_debug_fma_rate": (_I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
     "epic_image_host_async": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_timing_enable": (_I, [_P, _I]),
@@ -406,6 +407,13 @@ def epic_debug_grid(plan: Plan, d_volts, n_time: int, t: int, c: int, p: int, d_
     _check_size(d_grid, 8 * plan.info["grid_n"] ** 2, "d_grid")
     _check(load_library().epic_debug_grid(plan.handle, _ptr(d_volts), int(n_time), int(t), int(c), int(p),
                                           _ptr(d_grid), _stream(stream)), "epic_debug_grid")
+
+
+def epic_debug_transform(plan: Plan, d_volts, n_time: int, t: int, c: int, p: int, d_y, stream=None) -> None:
+    _check_size(d_volts, plan.volts_bytes(n_time), "d_volts")
+    _check_size(d_y, 8 * plan.info["grid_n"] ** 2, "d_y")
+    _check(load_library().epic_debug_transform(plan.handle, _ptr(d_volts), int(n_time), int(t), int(c), int(p),
+                                               _ptr(d_y), _stream(stream)), "epic_debug_transform")
 
 
 def epic_debug_fma_rate(iterations: int = 100000, stream=None) -> float:

@@ -88,6 +88,90 @@ def test_debug_grid_station_sample(torch, station):
     plan.close()
 
 
+def _round_f32(q):
+    """The float32 nearest to the rational q (ties to even), exactly."""
+    from fractions import Fraction
+    if q == 0:
+        return np.float32(0.0)
+    sign, q = (-1, -q) if q < 0 else (1, q)
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    scaled = q / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    n, rem = divmod(scaled.numerator, scaled.denominator)
+    twice = 2 * rem
+    if twice > scaled.denominator or (twice == scaled.denominator and n % 2 == 1):
+        n += 1
+    return np.float32(sign * n * 2.0 ** (e - 23))
+
+
+def _fma32(a, b, c):
+    """Elementwise a * b + c with a single rounding to float32 (a fused multiply-add)."""
+    from fractions import Fraction
+    out = np.empty(a.shape, np.float32)
+    for idx in np.ndindex(a.shape):
+        out[idx] = _round_f32(Fraction(float(a[idx])) * Fraction(float(b[idx])) + Fraction(float(c[idx])))
+    return out
+
+
+@pytest.mark.parametrize("case", GRID_CASES, ids=lambda c: f"s{c['seed']}")
+def test_debug_transform_matches_oracle(torch, case):
+    """The pre-square image Y of every (t, c, p): the imaging kernel's line
+    transforms against the oracle's direct transform of the oracle's grid."""
+    w = synth.random_small(**case)
+    plan = epic.plan_for(w)
+    arr = oracle_array(w)
+    dv = torch.from_numpy(w.volts).cuda()
+    y = torch.empty((w.grid_n, w.grid_n, 2), dtype=torch.float32, device="cuda")
+    for t in range(w.n_time):
+        for c in range(w.n_chan):
+            for p in range(w.n_pol):
+                epic.epic_debug_transform(plan, dv, w.n_time, t, c, p, y)
+                torch.cuda.synchronize()
+                got = y.cpu().numpy()
+                got = got[..., 0] + 1j * got[..., 1]
+                ref = oracle.dft2(oracle.grid(arr, w.volts, t, c, p))
+                assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max(), (t, c, p)
+    plan.close()
+
+
+def test_debug_transform_squares_to_the_imaged_sample(torch, station):
+    """For one sample without autocorrelation removal the imaging kernel's XX,
+    YY and XY are the products of the dumped transforms, bit for bit (same
+    gather order, same line transforms, same fused multiply-adds)."""
+    w = station
+    plan = epic.plan_for(w, subtract_autos=False)
+    for t in (0, 611):
+        dv = torch.from_numpy(np.ascontiguousarray(w.volts[t:t + 1])).cuda()
+        img = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+        epic.epic_image(plan, dv, 1, img, 0)
+        ys = []
+        for p in range(2):
+            y = torch.empty((w.grid_n, w.grid_n, 2), dtype=torch.float32, device="cuda")
+            epic.epic_debug_transform(plan, dv, 1, 0, 17, p, y)
+            ys.append(y)
+        torch.cuda.synchronize()
+        X, Y = ys[0].cpu().numpy(), ys[1].cpu().numpy()
+        im = img.cpu().numpy()[17]
+        zero = np.zeros_like(X[..., 0])
+        # XX = fma(x.re, x.re, fma(x.im, x.im, 0)): each fused multiply-add rounded once
+        assert np.array_equal(im[0], _fma32(X[..., 0], X[..., 0], _fma32(X[..., 1], X[..., 1], zero)))
+        assert np.array_equal(im[1], _fma32(Y[..., 0], Y[..., 0], _fma32(Y[..., 1], Y[..., 1], zero)))
+        assert np.array_equal(im[2], _fma32(X[..., 0], Y[..., 0], _fma32(X[..., 1], Y[..., 1], zero)))
+        assert np.array_equal(im[3], _fma32(X[..., 1], Y[..., 0], _fma32(-X[..., 0], Y[..., 1], zero)))
+    plan.close()
+
+
+def test_debug_transform_unsupported_plans(torch):
+    w = synth.random_small(1702, n_ant=6, n_pol=2, n_chan=1, grid_n=128, support=3, n_time=2)
+    plan = epic.plan_for(w)
+    y = torch.empty((128, 128, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_debug_transform(plan, torch.from_numpy(w.volts).cuda(), 2, 0, 0, 0, y)
+    assert ei.value.status == epic.EPIC_ERR_UNSUPPORTED
+    plan.close()
+
+
 # ------------------------------------------------------ whole path (A1-A7)
 def test_tiny_config(torch):
     w = synth.tiny()
