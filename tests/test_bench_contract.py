@@ -55,3 +55,15 @@ def test_traffic_records_are_reported_only_for_the_code_they_were_taken_on():
         assert os.path.exists(os.path.join(ROOT, rec["summary"])), name
         current = rec["source_sha"] == b.src_sha(rec["source"])
         assert b.dram_traffic(name) == (rec["bytes_per_launch"] if current else None), name
+
+
+def test_flop_model_matches_the_papers_grid_scaling():
+    """The FFT term of the benchmark's flop model grows as N^2 log2(N^2): from a
+    64^2 to a 128^2 grid by (128^2 x 14) / (64^2 x 12) = 4.67, the theoretical
+    factor the paper quotes for its grid-size scaling (Sec. 5)."""
+    b = _bench()
+    fft = lambda n: b.fp32_flops_per_tc(0, 1, n, 1) - n * n * 4  # one polarisation, no antennas
+    assert abs(fft(128) / fft(64) - (128 ** 2 * 14) / (64 ** 2 * 12)) < 1e-12
+    assert abs(fft(128) / fft(64) - 4.67) < 0.005
+    # and the station figure: 2 388 algorithmic flops per antenna-channel-sample on the 64^2 FP32 path
+    assert round(b.fp32_flops_per_tc(256, 2, 64, 5) / 256) == 2388
