@@ -56,7 +56,8 @@ typedef enum {
   EPIC_ERR_OOM = 4,         /* a device allocation failed                       */
   EPIC_ERR_CUDA = 5,        /* a CUDA call or launch failed                     */
   EPIC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up               */
-  EPIC_ERR_NO_DEVICE = 7    /* no usable CUDA device                            */
+  EPIC_ERR_NO_DEVICE = 7,   /* no usable CUDA device                            */
+  EPIC_ERR_INTERNAL = 8     /* a plan invariant does not hold (debug checks)    */
 } epic_status;
 
 /* How the 2-D spatial transform of Eq. (5) is computed. */
@@ -296,6 +297,16 @@ epic_status epic_debug_grid(epic_plan* plan, const uint8_t* d_volts, int n_time,
  * returns.  FP32 FFT plans with N = 32 or 64 (else EPIC_ERR_UNSUPPORTED). */
 epic_status epic_debug_transform(epic_plan* plan, const uint8_t* d_volts, int n_time, int t, int c, int p,
                                  float* d_y, void* stream);
+
+/* Debug: copies the plan's gridding tables to the host and checks them: every
+ * antenna, cell and entry index the imaging kernels dereference lies within
+ * the plan's sizes, each (warp, slot) range tiles its table set, and every
+ * lane's entry list equals the one re-derived from the per-cell table (the
+ * antennas whose kernel box covers the cell, in antenna order, folded with
+ * signs on folded grids), followed by weight-0 padding.  Writes a one-line
+ * summary or the first violated invariant to report (report_len bytes, may be
+ * NULL).  Returns EPIC_OK or EPIC_ERR_INTERNAL.  Synchronous. */
+epic_status epic_debug_check_plan(const epic_plan* plan, char* report, size_t report_len);
 
 /* Debug: the FP32 FMA rate the GPU sustains, measured by a kernel of
  * independent dependent-FMA chains filling every SM (2 flop per FMA).  One

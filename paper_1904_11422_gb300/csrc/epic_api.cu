@@ -205,6 +205,7 @@ const char* epic_status_string(int s) {
     case EPIC_ERR_CUDA: return "EPIC_ERR_CUDA";
     case EPIC_ERR_TIMEOUT: return "EPIC_ERR_TIMEOUT";
     case EPIC_ERR_NO_DEVICE: return "EPIC_ERR_NO_DEVICE";
+    case EPIC_ERR_INTERNAL: return "EPIC_ERR_INTERNAL";
     default: return "EPIC_ERR_UNKNOWN";
   }
 }

@@ -27,6 +27,7 @@ EPIC_ERR_OOM = 4
 EPIC_ERR_CUDA = 5
 EPIC_ERR_TIMEOUT = 6
 EPIC_ERR_NO_DEVICE = 7
+EPIC_ERR_INTERNAL = 8
 
 EPIC_XFORM_FFT_FP32 = 0
 EPIC_XFORM_DFT_BF16X3 = 1
@@ -89,6 +90,7 @@ SIGNATURES = {
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "epic_debug_transform": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "epic_debug_check_plan": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "epic_debug_fma_rate": (_I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
     "epic_image_host_async": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_timing_enable": (_I, [_P, _I]),
@@ -107,7 +109,8 @@ class EpicError(RuntimeError):
 
 def status_name(s: int) -> str:
     names = {0: "EPIC_OK", 1: "EPIC_ERR_INVALID_ARG", 2: "EPIC_ERR_OFFGRID", 3: "EPIC_ERR_UNSUPPORTED",
-             4: "EPIC_ERR_OOM", 5: "EPIC_ERR_CUDA", 6: "EPIC_ERR_TIMEOUT", 7: "EPIC_ERR_NO_DEVICE"}
+             4: "EPIC_ERR_OOM", 5: "EPIC_ERR_CUDA", 6: "EPIC_ERR_TIMEOUT", 7: "EPIC_ERR_NO_DEVICE",
+             8: "EPIC_ERR_INTERNAL"}
     return names.get(int(s), "EPIC_ERR_UNKNOWN")
 
 
@@ -414,6 +417,17 @@ def epic_debug_transform(plan: Plan, d_volts, n_time: int, t: int, c: int, p: in
     _check_size(d_y, 8 * plan.info["grid_n"] ** 2, "d_y")
     _check(load_library().epic_debug_transform(plan.handle, _ptr(d_volts), int(n_time), int(t), int(c), int(p),
                                                _ptr(d_y), _stream(stream)), "epic_debug_transform")
+
+
+def epic_debug_check_plan(plan: Plan) -> str:
+    """Host check of the plan's gridding tables (see include/epic.h); returns the
+    summary line, raises EpicError (EPIC_ERR_INTERNAL) with the first violated
+    invariant."""
+    buf = ctypes.create_string_buffer(512)
+    st = load_library().epic_debug_check_plan(plan.handle, buf, len(buf))
+    if st != EPIC_OK:
+        raise EpicError(st, f"epic_debug_check_plan: {buf.value.decode()}")
+    return buf.value.decode()
 
 
 def epic_debug_fma_rate(iterations: int = 100000, stream=None) -> float:

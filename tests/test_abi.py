@@ -61,7 +61,8 @@ def test_struct_layouts_match_header():
 
 def test_status_strings(lib):
     for code, name in [(0, "EPIC_OK"), (1, "EPIC_ERR_INVALID_ARG"), (2, "EPIC_ERR_OFFGRID"),
-                       (3, "EPIC_ERR_UNSUPPORTED"), (6, "EPIC_ERR_TIMEOUT"), (99, "EPIC_ERR_UNKNOWN")]:
+                       (3, "EPIC_ERR_UNSUPPORTED"), (6, "EPIC_ERR_TIMEOUT"), (7, "EPIC_ERR_NO_DEVICE"),
+                       (8, "EPIC_ERR_INTERNAL"), (99, "EPIC_ERR_UNKNOWN")]:
         assert epic.epic_status_string(code) == name
 
 
