@@ -2,6 +2,8 @@
 does not offer): for every gather-table layout the library builds, every index
 the imaging kernels dereference lies within the plan's sizes and every lane's
 entry list equals the one re-derived from the per-cell table."""
+import re
+
 import pytest
 
 from paper_1904_11422_gb300 import build_lib, epic, synth
@@ -37,6 +39,11 @@ def test_tables_hold_their_invariants(name, xf, grid_n, n_ant, support):
         assert plan.info["transforms_per_image"] == 4
     report = epic.epic_debug_check_plan(plan)
     assert report.startswith("ok:"), report
+    # the check walked every real entry: table sets x A x S^2 (four sets per channel when folded)
+    m = re.search(r"(\d+) table sets, (\d+) entries \((\d+) padding\)", report)
+    sets, entries, padding = (int(v) for v in m.groups())
+    assert sets == w.n_chan * plan.info["transforms_per_image"]
+    assert entries - padding == sets * n_ant * support ** 2
     plan.close()
 
 
