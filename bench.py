@@ -206,16 +206,19 @@ def _oracle_setup(w):
     return oracle, arr, oracle.max_threads()
 
 
-def _oracle_sample(oracle, arr, w, cores, target_s):
+def _oracle_sample(oracle, arr, w, cores, target_s, keep=None):
     """Grow a sample of the block (channels first up to the core count, then
     samples, then more channels) until one oracle run takes about target_s.
-    Returns (n_chan, n_time, seconds of the last run)."""
+    Returns (n_chan, n_time, seconds of the last run); keep (a dict), if given,
+    receives the last run's images."""
     n_c, n_t = min(cores, w.n_chan), 1
     while True:
         t0 = time.perf_counter()
-        oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
+        img = oracle.image(arr, w.volts[:n_t], subtract=True, c_lo=0, c_hi=n_c, use_fft=True, n_threads=cores)
         dt = time.perf_counter() - t0
         if dt >= 0.8 * target_s or (n_t == w.n_time and n_c == w.n_chan):
+            if keep is not None:
+                keep["image"] = img
             return n_c, n_t, dt
         grow = max(2.0, min(8.0, target_s / max(dt, 1e-3)))
         if n_t < w.n_time:
@@ -226,13 +229,33 @@ def _oracle_sample(oracle, arr, w, cores, target_s):
 
 def cpu_oracle_rate(w, seconds):
     """The FP64 oracle (FFT mode, as it stands) on a bounded sample of the block,
-    all host cores.  Returns (units/s, cores, sample description)."""
+    all host cores.  Returns (units/s, cores, sample description, (n_chan,
+    n_time, oracle images of the sample))."""
     oracle, arr, cores = _oracle_setup(w)
-    n_c, n_t, dt = _oracle_sample(oracle, arr, w, cores, seconds)
+    keep = {}
+    n_c, n_t, dt = _oracle_sample(oracle, arr, w, cores, seconds, keep)
     units = w.n_ant * n_c * n_t
     sample = (f"{n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block, "
               f"FP64 oracle FFT mode with autocorrelation removal, {cores} OpenMP threads, {dt:.1f} s")
-    return units / dt, cores, sample
+    return units / dt, cores, sample, (n_c, n_t, keep["image"])
+
+
+def measured_errors(epic, torch, w, dv, xforms, n_c, n_t, ref):
+    """Each transform's images of the oracle's sample (the first n_t samples,
+    channels 0 .. n_c-1) against the oracle's: max over channels and planes of
+    |GPU - oracle| / the channel's image peak max(|XX|, |YY|) of the oracle."""
+    import numpy as np
+    peak = np.maximum(np.abs(ref[:, 0]).max(axis=(1, 2)), np.abs(ref[:, 1]).max(axis=(1, 2)))
+    errs = {}
+    for xf in xforms:
+        plan = epic.plan_for(w, epic.XFORMS[xf], subtract_autos=True)
+        out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+        epic.epic_image(plan, dv[:n_t], n_t, out, 0)
+        epic.epic_sync(plan)
+        got = out[:n_c].double().cpu().numpy()
+        plan.close()
+        errs[xf] = float((np.abs(got - ref).max(axis=(1, 2, 3)) / peak).max())
+    return errs
 
 
 def _grow(run, n_max, target_s):
@@ -642,10 +665,16 @@ def main():
                 roof["fma_chain_tflops"] = fma
                 roof["fma_chain_of_peak"] = fma / roof["peak"]
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
+        rate, cores, sample, (n_c, n_t, ref) = cpu_oracle_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        # the GPU paths' images of the same sample against the oracle's images
+        xfs = [args.xform] + [x for x in args.paths.split(",") if x and x != args.xform]
+        accuracy = {"max_error_vs_oracle": measured_errors(epic, torch, w, copies[0], xfs, n_c, n_t, ref),
+                    "error_bound": {x: ERROR_BOUND.get(x) for x in xfs},
+                    "measure": "max over channels and planes of |GPU - FP64 oracle| / the channel's image peak",
+                    "sample": sample}
         if args.cpu_mode_seconds > 0:
             cpu["modes"] = cpu_oracle_modes(w, args.cpu_mode_seconds)
 
@@ -663,7 +692,7 @@ def main():
                                  f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
                 "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": primary["gpu_launches"], "kernel_times_ms": primary["kernel_times_ms"],
-                "paths": others, "grad": grad, "grid128": grid128, "batch": batch,
+                "paths": others, "grad": grad, "grid128": grid128, "batch": batch, "accuracy": accuracy,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
