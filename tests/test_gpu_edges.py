@@ -256,3 +256,33 @@ def test_async_host_call_rejects_pageable_buffers():
                                    np.empty(plan.out_shape, np.float32), 0)
     assert ei.value.status == epic.EPIC_ERR_INVALID_ARG
     plan.close()
+
+
+def test_plans_release_their_device_memory():
+    """Creating and destroying plans repeatedly (each used through the pipelined
+    host entry point, with per-launch timing on, and on the tensor path) returns
+    the device's free memory to where it started: no staging slot, stream, event
+    or table outlives its plan."""
+    import torch
+    w = synth.random_small(2130, n_ant=24, n_pol=2, n_chan=4, grid_n=64, support=3, n_time=12)
+    h_in = torch.from_numpy(w.volts).pin_memory()
+
+    def cycle():
+        for xf in ("fft_fp32", "dft_bf16x3"):
+            plan = epic.plan_for(w, epic.XFORMS[xf])
+            epic.epic_timing_enable(plan, True)
+            out = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+            for _ in range(3):
+                epic.epic_image_host_async(plan, h_in, w.n_time, out, 0)
+            epic.epic_sync(plan)
+            epic.epic_timing_read(plan)
+            plan.close()
+
+    cycle()  # first use: one-time allocations of the runtime and of the library
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(10):
+        cycle()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < 8 * 1024 * 1024, (free0, free1)
