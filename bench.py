@@ -693,6 +693,8 @@ def main():
                 "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": primary["gpu_launches"], "kernel_times_ms": primary["kernel_times_ms"],
                 "paths": others, "grad": grad, "grid128": grid128, "batch": batch, "accuracy": accuracy,
+                # seconds of data per block (40 us samples of 25 kHz channels) over seconds per block
+                "real_time_factor": (T * 40e-6) / (ms / args.steps / 1e3),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
