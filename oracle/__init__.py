@@ -14,7 +14,9 @@ from __future__ import annotations
 
 import contextlib
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 import threading
 
@@ -32,17 +34,35 @@ _INT = ctypes.POINTER(ctypes.c_int)
 _U8 = ctypes.POINTER(ctypes.c_uint8)
 
 
+_CMD = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-Wall",
+        "-Wno-unused-variable"]
+
+
+def _stamp() -> str:
+    """Hash of the source, the compile command and the host architecture."""
+    h = hashlib.sha256()
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(_CMD).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile ``libepic_oracle.so`` next to its source (gcc, OpenMP)."""
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
+    """Compile ``libepic_oracle.so`` next to its source (gcc, OpenMP), unless the
+    library there was built from the same source, command and architecture."""
+    stamp = _stamp()
+    stamp_path = _LIB_PATH + ".stamp"
+    if not force and os.path.exists(_LIB_PATH) and os.path.exists(stamp_path):
+        with open(stamp_path) as f:
+            if f.read().strip() == stamp:
+                return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-Wall", "-Wno-unused-variable",
-           _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(_CMD + [_SRC, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
+    with open(stamp_path + f".{os.getpid()}.tmp", "w") as f:
+        f.write(stamp + "\n")
+    os.replace(stamp_path + f".{os.getpid()}.tmp", stamp_path)
     return _LIB_PATH
 
 

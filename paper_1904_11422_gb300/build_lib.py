@@ -2,12 +2,18 @@
 
 Every translation unit under csrc/ is compiled in parallel with nvcc, then
 linked into ``paper_1904_11422_gb300/libepic.so`` (CUDA runtime linked
-statically).  Objects go to ``paper_1904_11422_gb300/_build/``.
+statically).  Objects go to ``paper_1904_11422_gb300/_build/``.  The library
+is rebuilt whenever the hash of its sources, headers, flags, compiler version
+and host architecture differs from the one recorded beside the objects, so a
+library copied from another machine or built from other sources is never
+reused.
 """
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -39,16 +45,41 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+_NVCC_VERSION: list[str] = []
+
+
+def _stamp() -> str:
+    """Hash of everything the library is built from: every source and header,
+    the public header, the compiler flags, the nvcc version and the host
+    architecture."""
+    h = hashlib.sha256()
+    deps = sorted(sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
+                  glob.glob(os.path.join(HERE, "..", "include", "*.h")))
+    for d in deps:
+        h.update(os.path.basename(d).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(_flags(False) + ARCH).encode())
+    if not _NVCC_VERSION:
+        _NVCC_VERSION.append(subprocess.run([nvcc(), "--version"], capture_output=True, text=True).stdout)
+    h.update(_NVCC_VERSION[0].encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+STAMP = os.path.join(BUILD, "libepic.stamp")
+
+
+def _stale(stamp: str) -> bool:
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
-    return any(os.path.getmtime(d) > t for d in deps)
+    with open(STAMP) as f:
+        return f.read().strip() != stamp
 
 
 def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) -> str:
-    if not force and not _stale():
+    stamp = _stamp()
+    if not force and not _stale(stamp):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     t0 = time.time()
@@ -75,6 +106,9 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}")
     os.replace(tmp, LIB)
+    with open(STAMP + f".{os.getpid()}.tmp", "w") as f:
+        f.write(stamp + "\n")
+    os.replace(STAMP + f".{os.getpid()}.tmp", STAMP)
     if not quiet:
         sys.stderr.write(f"libepic.so built in {time.time() - t0:.1f}s\n")
     return LIB

@@ -419,17 +419,31 @@ def test_beam_is_one_at_zero_frequency_and_bounded(oracle_lib):
     assert np.allclose(oracle.beam(arr1, 0), 1.0, atol=1e-14)
 
 
-def test_stokes_of_unpolarised_and_linear_sources(oracle_lib):
-    # closed forms: an unpolarised source (Y_X, Y_Y independent, equal power) has
-    # Q = U = V = 0 in expectation; a source with Y_Y = Y_X has I = 2 XX, Q = 0, U = I
+def _four_planes(yx, yy):
+    return np.stack([np.sum(np.abs(yx) ** 2, 0), np.sum(np.abs(yy) ** 2, 0),
+                     np.sum((yx * np.conj(yy)).real, 0), np.sum((yx * np.conj(yy)).imag, 0)])
+
+
+def test_stokes_of_unpolarised_linear_and_circular_sources(oracle_lib):
     rng = np.random.default_rng(5)
     N = 4
     yx = rng.standard_normal((200, N, N)) + 1j * rng.standard_normal((200, N, N))
-    img = np.stack([np.sum(np.abs(yx) ** 2, 0), np.sum(np.abs(yx) ** 2, 0),
-                    np.sum((yx * np.conj(yx)).real, 0), np.sum((yx * np.conj(yx)).imag, 0)])
+    # unpolarised: the incoherent sum of two orthogonal linear states, samples
+    # (s, s) and (s, -s): XX = YY and XY = 0 exactly, so Q = U = V = 0, I = 2 XX
+    yx_u = np.concatenate([yx, yx])
+    yy_u = np.concatenate([yx, -yx])
+    img = _four_planes(yx_u, yy_u)
+    st = oracle.stokes(img)
+    assert np.allclose(st[0], 2 * img[0]) and np.all(st[0] > 0)
+    assert np.allclose(st[1], 0) and np.allclose(st[2], 0) and np.allclose(st[3], 0)
+    # linear at 45 degrees: Y_Y = Y_X gives I = 2 XX, Q = 0, U = I, V = 0
+    img = _four_planes(yx, yx)
     st = oracle.stokes(img)
     assert np.allclose(st[0], 2 * img[0]) and np.allclose(st[1], 0) and np.allclose(st[2], st[0])
     assert np.allclose(st[3], 0)
+    # linear along x: Y_Y = 0 gives Q = I, U = V = 0
+    st = oracle.stokes(_four_planes(yx, 0 * yx))
+    assert np.allclose(st[1], st[0]) and np.allclose(st[2], 0) and np.allclose(st[3], 0)
     # circular: Y_Y = -i Y_X gives XY = Y_X conj(Y_Y) = i |Y_X|^2, so V = 2 |Y_X|^2 = I
     yy = -1j * yx
     img = np.stack([np.sum(np.abs(yx) ** 2, 0), np.sum(np.abs(yy) ** 2, 0),
