@@ -12,8 +12,12 @@ second (whole job).  Inputs are 4 rotating device copies of the block (164 MB,
 larger than L2).  ``--impl reference`` times the FP64 CPU oracle instead, on a
 bounded sample of the same block per step.
 
-Multi-GPU (torchrun): every rank images its own block with no collective in the
-data path (channels are independent), so per-GPU work is fixed ("weak").
+Multi-GPU: ``--gpus N`` starts N ranks itself (under torch.distributed.run on
+127.0.0.1) unless it already runs under a launcher.  ``--shard replicate``
+(default): every rank images its own block (per-GPU work fixed, "weak");
+``--shard channels``: the ranks split one block's channels (the paper's per-GPU
+bandwidth split, "strong").  Neither has a collective in the data path (channels
+are independent); the timing is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -44,6 +48,8 @@ N_COPIES = 4
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--shard", default="replicate", choices=["replicate", "channels"],
+                    help="multi-GPU: one block per rank (weak scaling) or one block's channels split (strong)")
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="epic", choices=["epic", "reference"])
@@ -69,6 +75,10 @@ def parse():
                     help="graph launches timed for the batching workload (0 to skip)")
     ap.add_argument("--grad-steps", type=int, default=20,
                     help="epic_grad calls timed on the gain-calibration config (0: skip)")
+    ap.add_argument("--accuracy-paths", default=ALL_XFORMS,
+                    help="transforms whose per-image errors against the oracle are reported at 64^2 and 128^2")
+    ap.add_argument("--accuracy128-seconds", type=float, default=10.0,
+                    help="oracle seconds for the 128^2 error sample (0: skip)")
     return ap.parse_args()
 
 
@@ -83,8 +93,10 @@ def fp32_flops_per_tc(A, P, N, S):
 
 
 # Error bound stated for each transform, relative to the channel's image peak
-# (checked against the FP64 oracle by the parity tests).
-ERROR_BOUND = {"fft_fp32": 1e-5, "dft_bf16x3": 1e-3, "dft_fp16x3": 1e-3, "dft_fp16": 5e-3, "dft_bf16": 2e-2}
+# (checked against the FP64 oracle by the parity tests, which state how each
+# was chosen).
+ERROR_BOUND = {"fft_fp32": 1e-5, "dft_bf16x3": 5e-5, "dft_fp16x3": 2e-5, "dft_fp16": 5e-3, "dft_bf16": 5e-2}
+ALL_XFORMS = "fft_fp32,dft_bf16x3,dft_fp16x3,dft_bf16,dft_fp16"
 
 
 def tensor_flops_per_tc(xform):
@@ -242,8 +254,10 @@ def cpu_oracle_rate(w, seconds):
 
 def measured_errors(epic, torch, w, dv, xforms, n_c, n_t, ref):
     """Each transform's images of the oracle's sample (the first n_t samples,
-    channels 0 .. n_c-1) against the oracle's: max over channels and planes of
-    |GPU - oracle| / the channel's image peak max(|XX|, |YY|) of the oracle."""
+    channels 0 .. n_c-1) against the oracle's: per image (channel c, plane XX,
+    YY, Re XY, Im XY), max |GPU - oracle| / the channel's image peak
+    max(|XX|, |YY|) of the oracle.  Returns {xform: {"max", "per_plane" (max over
+    channels), "per_channel" (max over planes), "bound"}}."""
     import numpy as np
     peak = np.maximum(np.abs(ref[:, 0]).max(axis=(1, 2)), np.abs(ref[:, 1]).max(axis=(1, 2)))
     errs = {}
@@ -254,8 +268,25 @@ def measured_errors(epic, torch, w, dv, xforms, n_c, n_t, ref):
         epic.epic_sync(plan)
         got = out[:n_c].double().cpu().numpy()
         plan.close()
-        errs[xf] = float((np.abs(got - ref).max(axis=(1, 2, 3)) / peak).max())
+        e = np.abs(got - ref).max(axis=(2, 3)) / peak[:, None]  # [C][4]
+        errs[xf] = {"max": float(e.max()), "bound": ERROR_BOUND.get(xf),
+                    "per_plane": [float(f"{x:.3g}") for x in e.max(axis=0)],
+                    "per_channel": [float(f"{x:.3g}") for x in e.max(axis=1)]}
     return errs
+
+
+def accuracy128(epic, torch, synth, xforms, seconds):
+    """The per-image errors of every transform on the station block at 128 x 128
+    against the oracle (FFT mode, all host cores) on a bounded sample of it."""
+    w = synth.station(grid_n=128)
+    oracle, arr, cores = _oracle_setup(w)
+    keep = {}
+    n_c, n_t, dt = _oracle_sample(oracle, arr, w, cores, seconds, keep)
+    dv = torch.from_numpy(w.volts).cuda()
+    errs = measured_errors(epic, torch, w, dv, xforms, n_c, n_t, keep["image"])
+    return {"errors": errs,
+            "sample": f"{n_c} channels x {n_t} samples x {w.n_ant} antennas of the station block on a 128x128 "
+                      f"grid, FP64 oracle FFT mode, {cores} OpenMP threads, {dt:.1f} s"}
 
 
 def _grow(run, n_max, target_s):
@@ -430,7 +461,12 @@ def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
         units = sum(w.units for w in ws)
         r = {"ms_per_launch": ms, "value": units * world / (ms / 1e3), "unit": UNIT, "units_per_launch": units,
              "xforms": dict(zip([w.name for w in ws], xforms)), "ctas_chosen": dict(zip([w.name for w in ws], b.ctas)),
-             "ms_separate_calls": ms_sep, "graph_launches_per_step": 1, "kernel_launches_per_step": 2 * len(plans)}
+             "ms_separate_calls": ms_sep, "graph_launches_per_step": 1,
+             # FP32 plans: an imaging kernel each (and a reduction); tensor-core plans of one
+             # transform: one persistent kernel that images them all (and, as the tuner
+             # chose, reduces them too, or leaves that to one reduction per plan)
+             "imaging_kernels_per_step": sum(x == "fft_fp32" for x in xforms)
+                                         + len({x for x in xforms if x != "fft_fp32"})}
         if name == "tensor":
             # issued tensor-core flops of the batch over the graph time (a 32^2
             # image set is one 64^2 transform, a 128^2 one four)
@@ -461,8 +497,27 @@ def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
     return res
 
 
+def torchrun_command(argv, n_gpus, port):
+    """The command that runs this script as n_gpus ranks on one node (one rank
+    per GPU, rendezvous on 127.0.0.1)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n_gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # started without a launcher: start the ranks (each sees WORLD_SIZE)
+        return subprocess.call(torchrun_command(sys.argv[1:], args.gpus, _free_port()))
     if args.impl == "reference":
         return run_reference(args)
 
@@ -484,7 +539,10 @@ def main():
     if dist is not None:
         dist.barrier()
 
-    w = synth.station()
+    block = synth.station()
+    # this rank's share of the band: the whole block, or its channel range of it
+    c_lo, c_hi = shard.rank_channels(block.n_chan, rank, world, args.shard)
+    w = block if (c_lo, c_hi) == (0, block.n_chan) else synth.channel_slice(block, c_lo, c_hi)
     T = w.n_time
     copies = [torch.from_numpy(w.volts).cuda() for _ in range(N_COPIES)]
     stream = torch.cuda.current_stream()
@@ -531,7 +589,7 @@ def main():
         epic.epic_timing_enable(plan, False)
         epic.epic_sync(plan)
         ms = shard.max_over_ranks(ms, device="cuda")
-        value = w.units * args.steps * world / (ms / 1e3)
+        value = shard.job_units(block.units, world, args.shard) * args.steps / (ms / 1e3)
         launches = sum(v[0] for v in kt.values())
         dom = max(kt.items(), key=lambda kv: kv[1][1])[0]
         n, tot = kt[dom]
@@ -565,7 +623,7 @@ def main():
         p2.close()
         others[xf] = r2
     clocks = sampler.stop()
-    units_step = w.units
+    units_step = shard.job_units(block.units, world, args.shard)
     value = primary["value"]
     ms = primary["ms_per_step"] * args.steps
 
@@ -595,7 +653,7 @@ def main():
             return shard.max_over_ranks(time.perf_counter() - t0, device="cuda")
 
         def rate(dt):
-            return units_step * args.e2e_steps * world / dt
+            return shard.job_units(block.units, world, args.shard) * args.e2e_steps / dt
 
         dt = timed_host(epic.epic_image_host_async, h_ins)
         dt_sync = timed_host(epic.epic_image_host, h_ins)
@@ -666,15 +724,20 @@ def main():
                 roof["fma_chain_of_peak"] = fma / roof["peak"]
 
     cpu, accuracy = None, None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and w is block:
         rate, cores, sample, (n_c, n_t, ref) = cpu_oracle_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-        # the GPU paths' images of the same sample against the oracle's images
-        xfs = [args.xform] + [x for x in args.paths.split(",") if x and x != args.xform]
-        accuracy = {"max_error_vs_oracle": measured_errors(epic, torch, w, copies[0], xfs, n_c, n_t, ref),
+        # every transform's images of the same sample against the oracle's images,
+        # per image (channel, plane), at 64 x 64 and on the 128 x 128 variant
+        xfs = [x for x in args.accuracy_paths.split(",") if x]
+        errs = measured_errors(epic, torch, w, copies[0], xfs, n_c, n_t, ref)
+        accuracy = {"max_error_vs_oracle": {x: e["max"] for x, e in errs.items()},
                     "error_bound": {x: ERROR_BOUND.get(x) for x in xfs},
-                    "measure": "max over channels and planes of |GPU - FP64 oracle| / the channel's image peak",
-                    "sample": sample}
+                    "measure": "per image (channel, plane): max over pixels of |GPU - FP64 oracle| / the "
+                               "channel's image peak; per_plane = max over channels, per_channel = max over planes",
+                    "grid64": {"errors": errs, "sample": sample}}
+        if args.accuracy128_seconds > 0:
+            accuracy["grid128"] = accuracy128(epic, torch, synth, xfs, args.accuracy128_seconds)
         if args.cpu_mode_seconds > 0:
             cpu["modes"] = cpu_oracle_modes(w, args.cpu_mode_seconds)
 
@@ -682,12 +745,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": value / PAPER_GTX980,
+                "scaling": shard.scaling(args.shard), "vs_baseline": value / PAPER_GTX980,
                 "dtype": "f32" if args.xform == "fft_fp32" else args.xform,
                 "data": "synthetic (seeded, LWA-station-shaped; no LWA-SV captures exist here)",
                 "config": {"workload": WORKLOAD, "xform": args.xform, "units_per_step": units_step,
                            "error_bound": ERROR_BOUND.get(args.xform),
-                           "parallelism": f"channel-independent blocks, one per GPU x {world}",
+                           "parallelism": (f"one block per GPU x {world}" if args.shard == "replicate" else
+                                           f"one block's 64 channels split over {world} GPUs"),
+                           "shard": args.shard,
                            "l2": f"inputs larger than L2: {N_COPIES} rotating device copies of the block "
                                  f"({N_COPIES * w.volts.nbytes / 1e6:.0f} MB)"},
                 "roofline": primary["roofline"], "cpu_baseline": cpu, "e2e": e2e,

@@ -186,16 +186,27 @@ epic_status epic_image_host_async(epic_plan* plan, const uint8_t* h_volts, int n
  * (The paper has no counterpart; it is an interface addition.)
  * Same arguments, layouts and results as epic_image (FP32 FFT plans only;
  * otherwise EPIC_ERR_UNSUPPORTED), computed by the same kernels with the same
- * summation order, but the per-call scratch (partial images and self powers)
- * comes from one static device array of EPIC_NOALLOC_SCRATCH_BYTES instead of
- * the plan's workspace, and no call allocates anything.
- *   - The plan's scratch need (epic_plan_info.workspace_bytes, rounded up to
- *     256-byte pieces) must fit in EPIC_NOALLOC_SCRATCH_BYTES; a plan that needs
- *     more is rejected with EPIC_ERR_UNSUPPORTED before anything is launched.
+ * work split and summation order, so the images equal epic_image's bit for
+ * bit.  The per-call scratch (partial images and self powers) comes from one
+ * static device array of EPIC_NOALLOC_SCRATCH_BYTES instead of the plan's
+ * workspace, and no call allocates anything.
+ *   - Scratch of a call: partial images slots x 4 x Ns^2 floats and self
+ *     powers slots x n_ant x 4 ints, each rounded up to a multiple of 256
+ *     bytes, where Ns is the side of a partial image (N, or N/2 when
+ *     info.transforms_per_image = 4) and slots = (CTAs or clusters of the
+ *     call's split) x (channels the busiest of them touches), at most
+ *     info.ctas x the plan's span count; the two together must fit in
+ *     EPIC_NOALLOC_SCRATCH_BYTES, else the call returns EPIC_ERR_UNSUPPORTED
+ *     before anything is launched.  The need never exceeds the partial-image
+ *     part of info.workspace_bytes and can be smaller for short blocks.
+ *   - Plans imaged by two-CTA clusters (info.cluster_dim = 2) also use the
+ *     row-exchange buffer the plan allocated when it was created.
  *   - The plan's device must be the current device (else EPIC_ERR_INVALID_ARG).
- *   - The first call on a device looks up the array's device address once
- *     (cudaGetSymbolAddress, which may load the library's device code); make that
- *     first call before any stream capture and before the time-critical loop.
+ *   - The first call with a device current looks up the array's device address
+ *     (cudaGetSymbolAddress, which may load the library's device code), and
+ *     looks it up again when the device's context has changed since (after
+ *     cudaDeviceReset); make that first call before any stream capture and
+ *     before the time-critical loop.
  *   - Every call, from every plan and stream, shares the one array: calls that
  *     overlap on the GPU race and corrupt each other's results.  Order them on
  *     one stream or synchronise between them.  The array keeps the previous
@@ -220,9 +231,11 @@ epic_status epic_image_noalloc(epic_plan* plan, const uint8_t* d_volts, int n_ti
  *   d_loss   device float: L
  * The gridded fields are recomputed in a second pass over the block rather than
  * stored (forward image, residual R = 2 (I - M), then per sample the conjugate
- * transform of R . Y degridded onto each antenna).  FP32 FFT plans with N = 64
- * and at most 512 antennas; others return EPIC_ERR_UNSUPPORTED.  Uses the
- * plan's workspace; asynchronous. */
+ * transform of R . Y degridded onto each antenna).  FP32 FFT plans with
+ * N = 32 and at most 128 antennas, N = 64 and at most 512, or N = 128 folded
+ * into four 64 x 64 problems (info.transforms_per_image = 4) and at most 512;
+ * others (tensor-core plans, 128 x 128 grids on two-CTA clusters) return
+ * EPIC_ERR_UNSUPPORTED.  Uses the plan's workspace; asynchronous. */
 epic_status epic_grad(epic_plan* plan, const uint8_t* d_volts, int n_time, const float* d_gains,
                       const float* d_model, float* d_grad, float* d_loss, void* stream);
 
@@ -248,20 +261,35 @@ epic_status epic_postprocess(const epic_plan* plan, const float* d_in, float* d_
  * sizes and channel counts, each with its own plan) run by one graph launch. */
 typedef struct epic_batch epic_batch;
 
-/* Captures the imaging launches of n_plans plans (distinct plans, 1..64) into
- * one CUDA graph, each plan on its own branch so the arrays run concurrently.
+/* Captures the imaging of n_plans plans (distinct plans, 1..64) into one CUDA
+ * graph, so that one launch images every array (the paper runs one pipeline per
+ * array; batching several is this library's addition, for arrays of uneven
+ * antenna count, grid size and channel count on one GPU).
  * d_volts[i], n_time[i], d_out[i] are plan i's arguments as in epic_image
  * (accumulate = 0); the pointers are baked into the graph and must stay valid
  * while the batch exists (their contents may change between launches).
- * tune = 1 runs the autotuner first: it times candidate graphs (each plan's
- * CTA count, i.e. its time-tile length: all SMs, shares proportional to the
- * plans' work, halved and quartered caps) and keeps the fastest; this launches
- * the imaging kernels several times on `stream` and overwrites d_out.
- * chosen_ctas (optional, [n_plans]) receives the CTA caps in the graph.
- * Synchronous.  Results equal epic_image's exactly when tune = 0, and up to the
- * summation order of the partial images (FP32 rounding) when tune = 1.  The
- * graph uses each plan's own workspace: a plan in a batch must not run other
- * calls (epic_image, epic_grad, another batch) concurrently with a launch. */
+ *   - Tensor-core plans of one transform form a family, imaged by ONE persistent
+ *     launch of one CTA per SM: every plan's call is cut into time tiles (W
+ *     consecutive (channel, sample) units), listed in a device work list
+ *     (largest tiles first), and claimed by the CTAs one at a time; each plan's
+ *     partial images are then reduced by its own small kernel.  The batch owns
+ *     these partial images.
+ *   - FP32 plans run their own imaging kernel and reduction, each plan on its
+ *     own graph branch so that the arrays overlap on the SMs.
+ * tune = 1 runs the autotuner first: it times candidate graphs (for FP32 plans
+ * each plan's CTA count, i.e. its time-tile length: all SMs, shares
+ * proportional to the plans' work, halved and quartered caps; for a tensor-core
+ * family its members' tile length: 1, 2, 3 or 4 tiles per SM and plan) and
+ * keeps the fastest; this launches the imaging kernels several times on
+ * `stream` and overwrites d_out.  chosen_ctas (optional, [n_plans]) receives
+ * each plan's CTA cap (FP32) or tile count cap (tensor core) in the graph.
+ * Synchronous.  Results equal epic_image's exactly when tune = 0 (every tile is
+ * the span one CTA of a single call images), and up to the summation order of
+ * the partial images (FP32 rounding) when tune = 1.  FP32 plans use their own
+ * workspace: a plan in a batch must not run other calls (epic_image,
+ * epic_grad, another batch) concurrently with a launch.  A bounded wait that
+ * gives up inside a family's launch is reported by epic_sync on the plan whose
+ * tile was being imaged. */
 epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_t* const* d_volts,
                               const int* n_time, float* const* d_out, int tune, int* chosen_ctas,
                               void* stream, epic_batch** out);
@@ -307,6 +335,20 @@ epic_status epic_debug_transform(epic_plan* plan, const uint8_t* d_volts, int n_
  * summary or the first violated invariant to report (report_len bytes, may be
  * NULL).  Returns EPIC_OK or EPIC_ERR_INTERNAL.  Synchronous. */
 epic_status epic_debug_check_plan(const epic_plan* plan, char* report, size_t report_len);
+
+/* Debug: the failure path of the tensor-core kernel's bounded waits.  (No
+ * counterpart in the paper: the test hook of the library's own failure
+ * detection.)  Runs the imaging kernel of a tensor-core plan over d_volts
+ * (layout as in epic_image, 1 <= n_time <= info.max_time) with the first
+ * mbarrier wait of every CTA made on a barrier that nothing ever arrives at,
+ * limited to wait_ns (1 000 .. 1 000 000 000).  Every CTA gives up on that
+ * wait, sets the plan's device status to a time-out, waits (bounded, one second)
+ * for the tensor-core products it has already issued, releases its tensor memory
+ * and returns; no output is written.  The next epic_sync(plan, stream) returns
+ * EPIC_ERR_TIMEOUT and clears the status, after which the plan and the device
+ * are usable as before.  EPIC_ERR_UNSUPPORTED for FP32 plans. */
+epic_status epic_debug_image_timeout(epic_plan* plan, const uint8_t* d_volts, int n_time, long long wait_ns,
+                                     void* stream);
 
 /* Debug: the FP32 FMA rate the GPU sustains, measured by a kernel of
  * independent dependent-FMA chains filling every SM (2 flop per FMA).  One

@@ -86,7 +86,7 @@ void free_plan(Plan& p) {
   void* ptrs[] = {p.d_ant_xy, p.d_freq, p.d_gains, p.d_delays, p.d_box, p.d_wx, p.d_wy, p.d_coef, p.d_coef64,
                   p.d_kx2, p.d_ky2, p.d_csr_ptr, p.d_csr_ent, p.d_twiddle, p.d_status, p.d_part, p.d_part_auto,
                   p.d_stage_in, p.d_stage_out, p.d_fmat, p.d_dphase, p.d_gcoef, p.d_gcoef64, p.d_gimage,
-                  p.d_resid, p.d_loss_part, p.d_gpart, p.d_beam, p.d_xbuf};
+                  p.d_resid, p.d_loss_part, p.d_gpart, p.d_beam, p.d_xbuf, p.d_dscale};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   epic::free_gather_tables(p.gt);
@@ -141,6 +141,9 @@ cudaError_t drain_timing(Plan& p) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+namespace epic {
 // Largest number of channels any CTA of a split touches.
 int spans_needed(const epic::WorkSplit& ws) {
   int worst = 1;
@@ -172,9 +175,6 @@ bool split_fits(const Plan& p, const epic::WorkSplit& ws) {
   return (long long)ws.ctas * ws.spans <= (long long)p.ctas * p.spans;
 }
 
-}  // namespace
-
-namespace epic {
 // The launches of one imaging call (image kernel, then the block-end reduction),
 // shared by epic_image and the batch graphs.  No timing, no allocation.
 cudaError_t image_launches(Plan& p, const uint8_t* d_volts, int n_time, float* d_out, int accumulate, cudaStream_t s) {
@@ -189,9 +189,8 @@ cudaError_t image_launches(Plan& p, const uint8_t* d_volts, int n_time, float* d
 }
 }  // namespace epic
 
-namespace {
-
-}  // namespace
+using epic::split_fits;
+using epic::split_work;
 
 extern "C" {
 
@@ -346,6 +345,8 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
     EPIC_TRY(epic::build_gather_tables(p, layout, 512, &gt_bytes));
     total += gt_bytes;
     EPIC_TRY(alloc(&p.d_fmat, (size_t)4 * 128 * 128 / 2, &total));
+    if (p.xform == EPIC_XFORM_DFT_FP16X3 || p.xform == EPIC_XFORM_DFT_FP16)
+      EPIC_TRY(alloc(&p.d_dscale, (size_t)4 * p.C * p.vq, &total));
     EPIC_TRY(epic::launch_dft_tables(p, 0));
     EPIC_TRY(cudaDeviceSynchronize());
     EPIC_TRY(epic::dft_image_config(p, &per_sm));
@@ -360,8 +361,11 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan** out) {
   if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128 && p.vq == 1)
     EPIC_TRY(alloc(&p.d_xbuf, epic::fft128_xbuf_elems(p.ctas, p.P), &total));
   p.workspace_bytes = total - before;
-  // epic_grad: FP32 FFT plans of 64 x 64 grids with one antenna per thread
-  if (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 64 && p.A <= 512 && epic::adjoint_smem_need(p) <= kSmemOptin) {
+  // epic_grad: FP32 FFT plans imaged by the fft_image kernel (32 x 32, 64 x 64,
+  // and 128 x 128 folded into four 64 x 64 problems), one antenna per thread of
+  // the adjoint (at most 128 antennas at 32 x 32, 512 otherwise)
+  if (p.xform == EPIC_XFORM_FFT_FP32 && (p.N != 128 || p.vq == 4) && p.A <= epic::adjoint_max_ant(p.N) &&
+      epic::adjoint_smem_need(p) <= kSmemOptin) {
     EPIC_TRY(alloc(&p.d_gcoef, C * A * P, &total));
     EPIC_TRY(alloc(&p.d_gcoef64, C * A * P, &total));
     EPIC_TRY(alloc(&p.d_gimage, C * 4 * N * N, &total));
@@ -528,6 +532,18 @@ epic_status epic_debug_transform(epic_plan* h, const uint8_t* d_volts, int n_tim
   if (h->p.xform != EPIC_XFORM_FFT_FP32 || (h->p.N != 32 && h->p.N != 64)) return EPIC_ERR_UNSUPPORTED;
   return from_cuda(epic::launch_debug_transform(h->p, d_volts, n_time, t, c, p, d_y,
                                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
+epic_status epic_debug_image_timeout(epic_plan* h, const uint8_t* d_volts, int n_time, long long wait_ns,
+                                     void* stream) {
+  if (!h || !d_volts || n_time < 1 || n_time > (1 << 24) || wait_ns < 1000 || wait_ns > 1000000000LL)
+    return EPIC_ERR_INVALID_ARG;
+  Plan& p = h->p;
+  if (p.xform == EPIC_XFORM_FFT_FP32) return EPIC_ERR_UNSUPPORTED;
+  const epic::WorkSplit ws = split_work(p, n_time);
+  if (!split_fits(p, ws)) return EPIC_ERR_UNSUPPORTED;
+  return from_cuda(epic::launch_dft_image(p, d_volts, n_time, ws, p.d_part, p.d_part_auto,
+                                          reinterpret_cast<cudaStream_t>(stream), (unsigned long long)wait_ns));
 }
 
 epic_status epic_timing_enable(epic_plan* h, int enable) {

@@ -5,7 +5,7 @@
 // With F[k][x] = exp(+2 pi i (k - N/2) x / N) (the pixel shift of reading R4
 // folded into the rows), one (t, c) image set is Y_g = F G_g F^T for the two
 // polarisation grids g.  Each complex product is one real GEMM with the 2N x 2N
-// matrix Fre = [[Fr, -Fi], [Fi, Fr]] (rows interleaved re/im) as the A operand:
+// matrix Fre = [[Fr, -Fi], [Fi, Fr]] (rows interleaved re/im by eights) as the A operand:
 //   stage 1 (along x): D1[(k,c)][(g,y)] = sum_(c',x) Fre[(k,c)][(c',x)] G[(g,y)][(c',x)]
 //   stage 2 (along y): D2[(j,c)][(g,k)] = sum_(c',y) Fre[(j,c)][(c',y)] Z[(g,k)][(c',y)]
 // where Z[(g,k)][(c,y)] = D1[(k,c)][(g,y)] is moved from tensor memory to shared
@@ -36,6 +36,7 @@
 
 #include "epic_internal.cuh"
 #include "epic_ptx.cuh"
+#include "epic_reduce.cuh"
 
 namespace epic {
 
@@ -47,6 +48,11 @@ constexpr int kN = 64;               // grid side of this kernel
 constexpr int kThreads = 512;        // 16 warps
 constexpr int kSlab = 128 * 128;     // one 128-row x 64-element 16-bit operand slab, bytes
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bounded waits: one second
+// FP16 operands: power-of-two scales keep every 16-bit value below 2^15
+// (FP16 overflows at 65 504) and the DFT matrix's low parts out of the
+// subnormal range; the scales are exact and undone in FP32 (see dft_scale_kernel).
+constexpr int kFp16MatExp = 12;      // the FP16 DFT matrix holds 2^12 F
+constexpr int kFp16TopExp = 15;      // gridded fields and stage-1 results scaled below 2^15
 
 // ---- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -65,13 +71,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of the given parity to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Waits for the phase of the given parity to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
+}
+// Waits until the counter at p reaches `expected` (acquire at GPU scope, so the
+// writes that preceded each increment are visible); false after limit_ns.
+__device__ __forceinline__ bool wait_count_bounded(const int* p, int expected, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    if (v >= expected) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+    __nanosleep(256);
+  }
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -184,14 +203,18 @@ struct DftSmem {
 // (layout kLayoutPairQ), the twiddle is applied to each gathered cell, and the
 // rest of the path is the 64 x 64 transform; the reduction interleaves the four
 // sub-images.
-template <int XF, bool Q128>
+// kBatch = false: one call of one plan, CTA b imaging span b of job0 (Q128 as
+// the plan's grid says).  kBatch = true: a persistent launch whose CTAs claim
+// the items of queue (spans of several plans' calls, 32 x 32, 64 x 64 and
+// 128 x 128 grids alike; Q128 is then read from each job) until none is left.
+// A_lay and max_entries size the shared-memory layout: the most antennas, and
+// the most gather entries held in shared memory, of any job.
+template <int XF, bool Q128, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1)
-    dft_image_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, long long W, long long units, int spans,
-                     const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
-                     const int* __restrict__ g_off, const uint16_t* __restrict__ g_task,
-                     const uint16_t* __restrict__ g_ent_a, const float* __restrict__ g_ent_w, int max_entries,
-                     int ent_in_smem, const uint32_t* __restrict__ fmat, const float2* __restrict__ twiddle,
-                     float* __restrict__ part, int* __restrict__ part_auto, int* __restrict__ status) {
+    dft_image_kernel(const __grid_constant__ DftJob job0, const __grid_constant__ DftQueue queue, int A_lay,
+                     int max_entries,
+                     const uint32_t* __restrict__ fmat, const float2* __restrict__ twiddle,
+                     unsigned long long test_wait_ns) {
   using Pr = Prec<XF>;
   constexpr bool kBf = Pr::kBf16;
   constexpr int NN = kN * kN;
@@ -201,24 +224,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* sm = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(sm);
   float4* E4 = reinterpret_cast<float4*>(sm + DftSmem::E);
-  float2* coef_s = reinterpret_cast<float2*>(E4 + A);       // [A][2]
-  int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A);    // [A]
-  float2* tw_s = reinterpret_cast<float2*>(auto_s + A);      // [128] exp(+2 pi i m / 128) (Q128)
+  float2* coef_s = reinterpret_cast<float2*>(E4 + A_lay);       // [A][2]
+  int4* auto_s = reinterpret_cast<int4*>(coef_s + 2 * A_lay);    // [A]
+  float2* tw_s = reinterpret_cast<float2*>(auto_s + A_lay);      // [128] exp(+2 pi i m / 128) (Q128)
   int* cnt_s = reinterpret_cast<int*>(tw_s + 128);           // [16 warps][8] trip counts
   int* base_s = cnt_s + 16 * 8;                              // [16 warps][8] first entries
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base_s + 16 * 8);  // stage 1, stage 2
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  // stage 1, stage 2, and a barrier nothing ever arrives at (the failure test)
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base_s + 16 * 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   float* entw_s = reinterpret_cast<float*>(abort_flag + 3);  // [max_entries]
   uint16_t* enta_s = reinterpret_cast<uint16_t*>(entw_s + max_entries);  // [max_entries]
+  int* claim_s = reinterpret_cast<int*>(abort_flag + 1);                  // batch: claimed item, wait result
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long u0 = (long long)blockIdx.x * W;
-  const long long u1 = min(u0 + W, units);
-  if (u0 >= u1) return;
-  const int c_first = (int)(u0 / T);
-  const uint32_t bar1 = smem_u32(&bars[0]), bar2 = smem_u32(&bars[1]);
-  if constexpr (Q128)
+  if (!kBatch && (long long)blockIdx.x * job0.W >= job0.units) return;
+  const uint32_t bar1 = smem_u32(&bars[0]), bar2 = smem_u32(&bars[1]), bar_never = smem_u32(&bars[2]);
+  if (Q128 || (kBatch && twiddle))
     for (int m = tid; m < 128; m += kThreads) tw_s[m] = twiddle[m];
 
   // ---- set-up: TMEM, mbarriers, the DFT matrix into TMEM ----
@@ -230,6 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     mbar_init(bar1, 1);
     mbar_init(bar2, 1);
+    mbar_init(bar_never, 1);
     fence_mbar_init();
     *abort_flag = 0;
   }
@@ -256,11 +279,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
 
-  uint32_t ph1 = 0, ph2 = 0, pend1 = 0, pend2 = 0;
+  // the job and span being imaged (set per item; read through a pointer, so that
+  // the job's fields stay in parameter or global memory rather than registers)
+  const DftJob* jp = &job0;
+  long long b_item = blockIdx.x, u0 = 0, u1 = 0;
+  int c_first = 0;
+  bool q128 = Q128;
+
+  uint32_t ph1 = 0, ph2 = 0;
+  uint32_t n_commit1 = 0, n_commit2 = 0;  // MMA groups committed to each barrier (every thread counts)
+  bool first_wait = true;
   int d2buf = 0, have_prev = 0, prev_buf = 0;
   int pair[4] = {0, 0, 0, 0};                            // gridder: four cell pairs (y, 2r..2r+1), index y*32 + r
-  const int ej = 16 * lg + (lane >> 1), ec = lane & 1;   // epilogue lanes (j, c) of D2
-  const int ck = 16 * lg + (lane >> 1), cc = lane & 1;   // conversion lanes (k, c) of D1
+  // TMEM lane m = 32 lg + lane holds output row k = 8 (m >> 4) + (m & 7), part
+  // c = (m >> 3) & 1 (real, imaginary) of D1 and D2 (see dft_matrix_kernel)
+  const int ej = 16 * lg + 8 * (lane >> 4) + (lane & 7), ec = (lane >> 3) & 1;  // epilogue lanes (j, c) of D2
+  const int ck = ej, cc = ec;                                                   // conversion lanes (k, c) of D1
   const int cg = cq >> 1, cy0 = 32 * (cq & 1);           // conversion columns (g, y0 .. y0+31)
 
   float acc[4][8];
@@ -268,29 +302,49 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
     for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
+  // FP16 transforms: the channel's power-of-two scales of the gridded fields and
+  // of the stage-1 result, and the factor that undoes both (and the DFT
+  // matrix's) on the squares
+  float sc_g = 1.f, sc_z = 1.f, sc_out = 1.f;
 
-  auto wait_or_abort = [&](uint32_t bar, uint32_t& ph, uint32_t& pend) {
-    if (!mbar_wait_bounded(bar, ph)) {
-      atomicExch(status, kDevTimeout);
+  // Bounded wait for the next phase of a barrier; on time-out the plan's status
+  // word and the CTA's abort flag are set (read by every thread after the next
+  // CTA barrier).  With test_wait_ns, the CTA's first wait is instead made on a
+  // barrier that nothing arrives at, limited to test_wait_ns: a time-out that
+  // is certain to happen, for testing this path.
+  auto wait_or_abort = [&](uint32_t bar, uint32_t& ph) -> bool {
+    bool ok;
+    if (test_wait_ns && first_wait) ok = mbar_wait_bounded(bar_never, 0, test_wait_ns);
+    else ok = mbar_wait_bounded(bar, ph);
+    first_wait = false;
+    if (!ok) {
+      atomicExch(jp->status, kDevTimeout);
       *abort_flag = 1;
     }
-    pend = ph;
     ph ^= 1;
     tc_fence_after();
+    return ok;
   };
 
   // squaring and accumulation of one stage-2 result (TMEM lanes (j, c), columns
-  // (g, k)); partner lanes 2j / 2j+1 exchange the other component
-  auto epilogue = [&](int buf) {
+  // (g, k)); partner lanes (lane ^ 8: same j, other c) exchange the other component
+  // (tensor memory is read only by warps all of whose threads saw the products
+  // complete; after a time-out the warp squares zeros instead)
+  auto epilogue = [&](int buf, bool ok) {
     float X[16], Y[16];
     const uint32_t d2 = tmem + lane_base + kColD2 + 128 * buf;
-    tmem_ld16(d2 + 16 * cq, X);
-    tmem_ld16(d2 + 64 + 16 * cq, Y);
-    tmem_wait_ld();
+    if (__all_sync(0xffffffffu, ok)) {
+      tmem_ld16(d2 + 16 * cq, X);
+      tmem_ld16(d2 + 64 + 16 * cq, Y);
+      tmem_wait_ld();
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) X[k] = Y[k] = 0.f;
+    }
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const float sx = ec ? X[s] : X[8 + s], sy = ec ? Y[s] : Y[8 + s];
-      const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
+      const float rx = __shfl_xor_sync(0xffffffffu, sx, 8), ry = __shfl_xor_sync(0xffffffffu, sy, 8);
       const float xr = ec ? rx : X[s], xi = ec ? X[8 + s] : rx;
       const float yr = ec ? ry : Y[s], yi = ec ? Y[8 + s] : ry;
       acc[0][s] = fmaf(xr, xr, fmaf(xi, xi, acc[0][s]));
@@ -302,29 +356,30 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   auto flush = [&](int c) {
     const int slot = c - c_first;
-    float* dst = part + (size_t)((long long)blockIdx.x * spans + slot) * 4 * NN;
+    float* dst = jp->part + (size_t)(b_item * jp->spans + slot) * 4 * NN;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int k = 16 * cq + 8 * ec + s;
 #pragma unroll
-      for (int pl = 0; pl < 4; ++pl) dst[(size_t)pl * NN + ej * kN + k] = acc[pl][s];
+      for (int pl = 0; pl < 4; ++pl) dst[(size_t)pl * NN + ej * kN + k] = kBf ? acc[pl][s] : acc[pl][s] * sc_out;
     }
-    int4* pa = reinterpret_cast<int4*>(part_auto) + (size_t)((long long)blockIdx.x * spans + slot) * A;
-    for (int a = tid; a < A; a += kThreads) pa[a] = auto_s[a];
+    int4* pa = reinterpret_cast<int4*>(jp->part_auto) + (size_t)(b_item * jp->spans + slot) * jp->A;
+    for (int a = tid; a < jp->A; a += kThreads) pa[a] = auto_s[a];
   };
 
   // the two bytes of each of the thread's antennas (a = tid + 512 k < A <= 1024),
   // prefetched one sample ahead so that the unpack never waits for HBM; packed
   // as antenna tid in the low and antenna tid + 512 in the high half
   auto load_raw = [&](long long u) -> unsigned {
-    const int c = (int)(u / T), t = (int)(u % T);
-    const int cr = Q128 ? c >> 2 : c;
-    const unsigned short* base = reinterpret_cast<const unsigned short*>(volts + ((size_t)t * C + cr) * (size_t)A * 2);
-    unsigned r = tid < A ? (unsigned)__ldg(base + tid) : 0u;
-    if (tid + kThreads < A) r |= (unsigned)__ldg(base + tid + kThreads) << 16;
+    const int c = (int)(u / jp->T), t = (int)(u % jp->T);
+    const int cr = q128 ? c >> 2 : c;
+    const unsigned short* base =
+        reinterpret_cast<const unsigned short*>(jp->volts + ((size_t)t * jp->C + cr) * (size_t)jp->A * 2);
+    unsigned r = tid < jp->A ? (unsigned)__ldg(base + tid) : 0u;
+    if (tid + kThreads < jp->A) r |= (unsigned)__ldg(base + tid + kThreads) << 16;
     return r;
   };
-  unsigned raw = load_raw(u0), raw_next = 0;
+  unsigned raw = 0, raw_next = 0;
   const uint16_t* ent_a = enta_s;
   const float* ent_w = entw_s;
 
@@ -334,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int h = 0; h < 2; ++h) {
       const int a = tid + h * kThreads;
       const unsigned rb = h ? rw >> 16 : rw & 0xffffu;
-      if (a < A) {
+      if (a < jp->A) {
         const int xr = nib_hi(rb & 0xffu), xi = nib_lo(rb & 0xffu);
         const int yr = nib_hi(rb >> 8), yi = nib_lo(rb >> 8);
         const float2 kx = coef_s[2 * a], ky = coef_s[2 * a + 1];
@@ -351,45 +406,103 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
   bool have_next = false;  // E already holds this sample (unpacked while stage 1 ran)
   int cur_c = -1;
+  for (int it = 0;; ++it) {
+    // ---- the next item: this CTA's span, or the next unclaimed one of the queue
+    if constexpr (!kBatch) {
+      if (it > 0) break;
+    } else {
+      __syncthreads();  // every thread has read the previous claim and the abort flag is settled
+      if (*abort_flag) break;
+      if (tid == 0) *claim_s = atomicAdd(queue.head, 1);
+      __syncthreads();
+      const int item = *claim_s;
+      if (item >= queue.n_items) break;
+      if (item >= queue.n_image_items) {
+        // ---- a reduction item: rows of one virtual channel of one job, once
+        // every imaging item that wrote a partial image of it has signalled
+        int k = 0;
+        while (k + 1 < queue.n_jobs && item >= queue.jobs[k + 1].red_first) ++k;
+        const DftJob& rj = queue.jobs[k];
+        const int L = rj.red.vq == 4 ? rj.red.N / 2 : rj.red.N;
+        const int piece = item - rj.red_first, per_cv = L / rj.red_rows;
+        const int cv = piece / per_cv, j0 = (piece % per_cv) * rj.red_rows;
+        if (tid == 0) {
+          const long long b_lo = ((long long)cv * rj.red.T) / rj.red.W;
+          const long long b_hi = min(((long long)(cv + 1) * rj.red.T - 1) / rj.red.W, (long long)rj.red.ctas - 1);
+          const bool ok = wait_count_bounded(rj.done + cv, (int)(b_hi - b_lo + 1), kWaitNs);
+          if (!ok) atomicExch(rj.status, kDevTimeout);
+          claim_s[1] = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (claim_s[1]) reduce_rows<2, kBatchReducePix>(rj.red, cv, j0, rj.red_rows, tid, kThreads, sm);
+        continue;
+      }
+      int k = 0;
+      while (k + 1 < queue.n_jobs && item >= queue.jobs[k + 1].first_item) ++k;
+      jp = &queue.jobs[k];
+      b_item = item - jp->first_item;
+      q128 = jp->q128 != 0;
+    }
+    u0 = b_item * jp->W;
+    u1 = min(u0 + jp->W, jp->units);
+    if (u0 >= u1) continue;
+    c_first = (int)(u0 / jp->T);
+    raw = load_raw(u0);
+    have_next = false;
+    cur_c = -1;
   for (long long u = u0; u < u1; ++u) {
-    const int c = (int)(u / T);
+    const int c = (int)(u / jp->T);
     if (c != cur_c) {
       if (have_prev) {  // the last sample of the previous channel still owes its squares
-        wait_or_abort(bar2, ph2, pend2);
-        epilogue(prev_buf);
+        const bool ok2 = wait_or_abort(bar2, ph2);
+        epilogue(prev_buf, ok2);
         have_prev = 0;
       }
+      const int flushed = cur_c;
       if (cur_c >= 0) {
         flush(cur_c);
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
           for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
+        if constexpr (kBatch) __threadfence();  // the partial image is visible GPU-wide before the signal
       }
       cur_c = c;
       tc_fence_before();
       __syncthreads();
-      const int cr = Q128 ? c >> 2 : c;
-      for (int k = tid; k < 2 * A; k += kThreads) coef_s[k] = coef[(size_t)cr * A * 2 + k];
-      for (int a = tid; a < A; a += kThreads) auto_s[a] = make_int4(0, 0, 0, 0);
-      if (tid < 16 * 8) {
-        cnt_s[tid] = g_cnt[(size_t)c * 16 * 8 + tid];
-        base_s[tid] = g_base[(size_t)c * 16 * 8 + tid];
+      if (kBatch && flushed >= 0 && tid == 0) atomicAdd(jp->done + flushed, 1);
+      const int cr = q128 ? c >> 2 : c;
+      if constexpr (!kBf) {
+        const float4 sc = jp->dscale[c];
+        sc_g = sc.x;
+        sc_z = sc.y;
+        sc_out = sc.z;
       }
-      const int e0 = g_off[c], ne = g_off[c + 1] - e0;
-      if (ent_in_smem) {
+      // (FP16: the fields' scale rides on the coefficients, exactly: a power of two)
+      for (int k = tid; k < 2 * jp->A; k += kThreads) {
+        float2 v = jp->coef[(size_t)cr * jp->A * 2 + k];
+        if constexpr (!kBf) v = make_float2(v.x * sc_g, v.y * sc_g);
+        coef_s[k] = v;
+      }
+      for (int a = tid; a < jp->A; a += kThreads) auto_s[a] = make_int4(0, 0, 0, 0);
+      if (tid < 16 * 8) {
+        cnt_s[tid] = jp->cnt[(size_t)c * 16 * 8 + tid];
+        base_s[tid] = jp->base[(size_t)c * 16 * 8 + tid];
+      }
+      const int e0 = jp->off[c], ne = jp->off[c + 1] - e0;
+      if (jp->ent_in_smem) {
         for (int k = tid; k < ne; k += kThreads) {
-          enta_s[k] = g_ent_a[e0 + k];
-          entw_s[k] = g_ent_w[e0 + k];
+          enta_s[k] = jp->ent_a[e0 + k];
+          entw_s[k] = jp->ent_w[e0 + k];
         }
         ent_a = enta_s;
         ent_w = entw_s;
       } else {
-        ent_a = g_ent_a + e0;
-        ent_w = g_ent_w + e0;
+        ent_a = jp->ent_a + e0;
+        ent_w = jp->ent_w + e0;
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) pair[j] = g_task[((size_t)c * kThreads + tid) * 4 + j];
+      for (int j = 0; j < 4; ++j) pair[j] = jp->task[((size_t)c * kThreads + tid) * 4 + j];
       __syncthreads();
     }
 
@@ -427,11 +540,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         gre[0][s] = xr; gim[0][s] = xi; gre[1][s] = yr; gim[1][s] = yi;
       }
       };
-      if (ent_in_smem)
+      if (jp->ent_in_smem)
         gather(enta_s, entw_s);
       else
         gather(ent_a, ent_w);
-      if constexpr (Q128) {
+      if (q128) {
         // H_q = exp(+2 pi i (alpha x + beta y) / 128) x the folded gather
         const int alpha = cur_c & 1, beta = (cur_c >> 1) & 1;
 #pragma unroll
@@ -487,15 +600,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       mma_commit(bar1);
     }
+    ++n_commit1;
 
     // 4. while stage 1 runs: squares of the previous sample, and the next
     //    sample's fields if it is of the same channel (every thread has
     //    finished the gather that read E)
     if (have_prev) {
-      wait_or_abort(bar2, ph2, pend2);
-      epilogue(prev_buf);
+      const bool ok2 = wait_or_abort(bar2, ph2);
+      epilogue(prev_buf, ok2);
     }
-    if (u + 1 < u1 && (int)((u + 1) / T) == c) {
+    if (u + 1 < u1 && (int)((u + 1) / jp->T) == c) {
       unpack(raw_next);
       have_next = true;
     }
@@ -507,14 +621,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     //    in two halves along K: a thread's first 16 y values are the K steps
     //    0, 2, 4, 6, its last 16 the steps 1, 3, 5, 7, so the products of the
     //    first half run while the second half is converted.
-    wait_or_abort(bar1, ph1, pend1);
+    const bool ok1 = wait_or_abort(bar1, ph1);
     uint32_t accum2 = 0;
     const uint32_t d1 = tmem + lane_base + kColD1 + 32 * cq;
     const int zrow = cg * kN + ck;
     auto convert_z = [&](int half) {
       float v[16];
-      tmem_ld16(d1 + 16 * half, v);
-      tmem_wait_ld();
+      if (__all_sync(0xffffffffu, ok1)) {
+        tmem_ld16(d1 + 16 * half, v);
+        tmem_wait_ld();
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+      }
+      if constexpr (!kBf) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] *= sc_z;
+      }
 #pragma unroll
       for (int qq = 0; qq < 2; ++qq) {
         uint32_t hi[4], lo[4];
@@ -554,6 +677,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (half == 1) mma_commit(bar2);
       }
+      if (half == 1) ++n_commit2;
     };
     convert_z(0);
     if (*abort_flag) break;  // no wait lies between here and the commit below
@@ -565,18 +689,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     d2buf ^= 1;
     raw = raw_next;
   }
-  if (!*abort_flag) {
-    if (have_prev) {
-      wait_or_abort(bar2, ph2, pend2);
-      epilogue(prev_buf);
-    }
-    if (cur_c >= 0) flush(cur_c);
+  // ---- end of the item: the last sample's squares, then its channel's partial
+  if (*abort_flag) break;  // read after the loop's last CTA barrier: every thread agrees
+  if (have_prev) {
+    const bool ok2 = wait_or_abort(bar2, ph2);
+    epilogue(prev_buf, ok2);
+    have_prev = 0;
+  }
+  if (cur_c >= 0) flush(cur_c);
+  if constexpr (kBatch) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0 && cur_c >= 0) atomicAdd(jp->done + cur_c, 1);
+  }
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
   }
   // after a timed-out wait the MMAs may still be running: one more bounded wait
-  // on each barrier before the tensor memory they write is released
+  // for the last group committed to each barrier before the tensor memory they
+  // write is released.  Each barrier is at most one phase behind: a group is
+  // committed only after the wait for the barrier's previous group succeeded
+  // (after a time-out the loop issues at most the current sample's stage 1,
+  // whose barrier's previous wait did succeed, and leaves before stage 2)
   if (*abort_flag) {
-    mbar_wait_bounded(bar1, pend1);
-    mbar_wait_bounded(bar2, pend2);
+    if (n_commit1) mbar_wait_bounded(bar1, (n_commit1 - 1) & 1);
+    if (n_commit2) mbar_wait_bounded(bar2, (n_commit2 - 1) & 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -587,21 +726,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---- plan-time tables ----------------------------------------------------------
-// The real 2N x 2N DFT matrix [[Fr, -Fi], [Fi, Fr]] with rows m = 2k + c (c = 0
-// real, 1 imaginary output part) and columns K = c' N + x, split into 16-bit hi
+// The real 2N x 2N DFT matrix [[Fr, -Fi], [Fi, Fr]] with rows
+// m = 16 (k / 8) + 8 c + k % 8 (c = 0 real, 1 imaginary output part: eight
+// output rows k in a row, so that the eight threads of a 16-byte store phase of
+// the stage-1 conversion write eight consecutive rows of one slab, free of
+// bank conflicts) and columns K = c' N + x, split into 16-bit hi
 // and lo parts in FP64, stored row-major as packed pairs (element K in the low
-// half of word K/2 when K is even): [2 (hi, lo)][128 rows][64 words].
+// half of word K/2 when K is even): [2 (hi, lo)][128 rows][64 words].  The FP16
+// matrix is scaled by 2^kFp16MatExp, so that its low parts (up to 2^-12 of an
+// entry) stay clear of FP16's subnormal range.
 template <bool kBf16>
 __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
   const int m = blockIdx.x;          // 0..127
   const int kk = threadIdx.x;        // 0..127
-  const int k = m >> 1, c = m & 1, cp = kk >> 6, x = kk & 63;
+  const int k = 8 * (m >> 4) + (m & 7), c = (m >> 3) & 1, cp = kk >> 6, x = kk & 63;
   const int f = k - kN / 2;
   const int ph = (((f * x) % kN) + kN) % kN;
   double sn, cs;
   sincospi(2.0 * (double)ph / (double)kN, &sn, &cs);
   // output re = Fr Gr - Fi Gi ; output im = Fi Gr + Fr Gi
-  const double v = (c == 0) ? (cp == 0 ? cs : -sn) : (cp == 0 ? sn : cs);
+  const double v = ldexp((c == 0) ? (cp == 0 ? cs : -sn) : (cp == 0 ? sn : cs), kBf16 ? 0 : kFp16MatExp);
   uint16_t hi, lo;
   if (kBf16) {
     const __nv_bfloat16 h = __double2bfloat16(v);
@@ -616,32 +760,132 @@ __global__ void dft_matrix_kernel(uint16_t* __restrict__ out) {
   out[(size_t)128 * 128 + (size_t)m * 128 + kk] = lo;
 }
 
+// Power-of-two scales of the FP16 transforms, per virtual channel: bounds on
+// the 64 x 64 field each virtual channel transforms (the grid itself, its four
+// quadrants folded for a 128 x 128 grid, or a zero-padded 32 x 32 grid).  With
+// cb(y, x) = 8 sqrt(2) sum_{a covering the field cell} |w_a| max_p |k_a,p| >=
+// |G(y, x)| (a 4+4-bit sample has modulus at most 8 sqrt(2)),
+//   bound_G = max_(y,x) cb,   bound_Z = max_y sum_x cb >= |stage-1 result|
+// (every DFT matrix entry has modulus 1).  The fields are scaled by
+// s_g = 2^(15 - e(bound_G)) and the stage-1 result (which carries s_g and the
+// matrix's 2^12) by s_z = 2^(15 - e(2^12 s_g bound_Z)), where 2^e(b) is the
+// next power of two above b, so that every 16-bit operand stays below 2^15;
+// the squares of the stage-2 result carry (2^24 s_g s_z)^2, undone in FP32 by
+// s_out.  All three are exact powers of two.
+__global__ void dft_scale_kernel(int A, int P, int N, int S, int vq, const int* __restrict__ csr_ptr,
+                                 const int2* __restrict__ csr_ent, const double2* __restrict__ coef64,
+                                 float4* __restrict__ out) {
+  __shared__ double row_sum[kN], row_max[kN];
+  const int c = blockIdx.x, fy = threadIdx.x;  // one thread per field row
+  const int NN = N * N;
+  const int* ptr = csr_ptr + (size_t)c * (NN + 1);
+  const int2* ent = csr_ent + (size_t)c * A * S * S;
+  const double2* k = coef64 + (size_t)c * A * P;
+  if (fy < kN) {
+    double rs = 0.0, rm = 0.0;
+    for (int fx = 0; fx < kN; ++fx) {
+      double cb = 0.0;
+      const int reps = (N == 128) ? 4 : 1;
+      for (int r = 0; r < reps; ++r) {
+        const int y = fy + kN * (r >> 1), x = fx + kN * (r & 1);
+        if (y >= N || x >= N) continue;  // a 32 x 32 grid padded to 64 x 64
+        for (int e = ptr[y * N + x]; e < ptr[y * N + x + 1]; ++e) {
+          const int2 en = ent[e];
+          double km = 0.0;
+          for (int p = 0; p < P; ++p) km = fmax(km, hypot(k[(size_t)en.x * P + p].x, k[(size_t)en.x * P + p].y));
+          cb += fabs((double)__int_as_float(en.y)) * km;
+        }
+      }
+      cb *= 8.0 * 1.4142135623730951;
+      rs += cb;
+      rm = fmax(rm, cb);
+    }
+    row_sum[fy] = rs;
+    row_max[fy] = rm;
+  }
+  __syncthreads();
+  if (fy == 0) {
+    double bg = 0.0, bz = 0.0;
+    for (int y = 0; y < kN; ++y) {
+      bg = fmax(bg, row_max[y]);
+      bz = fmax(bz, row_sum[y]);
+    }
+    // 2^e above b: frexp gives b = m 2^e with m in [0.5, 1); a zero bound needs no scale
+    int eg = 0, ez = 0;
+    if (bg > 0.0) frexp(bg, &eg);
+    const int sg = max(-100, min(100, kFp16TopExp - eg));
+    if (bz > 0.0) frexp(ldexp(bz, kFp16MatExp + sg), &ez);
+    int sz = max(-100, min(100, kFp16TopExp - ez));
+    // the squares' factor 2^(-2 (2 * 12 + sg + sz)) must stay a normal FP32
+    const int tot = max(-60, min(60, 2 * kFp16MatExp + sg + sz));
+    sz = tot - 2 * kFp16MatExp - sg;
+    const float4 v = make_float4(ldexpf(1.f, sg), ldexpf(1.f, sz), ldexpf(1.f, -2 * tot), 0.f);
+    for (int q = 0; q < vq; ++q) out[(size_t)c * vq + q] = v;
+  }
+}
+
 size_t dft_smem_bytes(int A, int max_entries) {
   size_t b = 8 * (size_t)kSlab;            // the two B operands (gridded fields, stage-1 result)
   b += 16 * (size_t)A + 16 * (size_t)A + 16 * (size_t)A;  // E, coefficients, self powers
   b += 128 * sizeof(float2);                // twiddles of the 128 x 128 split
   b += 2 * 16 * 8 * sizeof(int);            // gather trip counts and bases
-  b += 32;                                  // two mbarriers, TMEM address, abort flag
+  b += 40;                                  // three mbarriers, TMEM address, abort flag
   b += 6 * (size_t)max_entries;             // gather entries (weight, antenna)
   return b + 1024;                          // alignment slack
 }
 
+// The job of one call of plan p over T samples with split ws.
+DftJob job_of(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part, int* part_auto) {
+  DftJob j{};
+  j.volts = d_volts;
+  j.coef = p.d_coef;
+  j.cnt = p.gt.d_cnt;
+  j.base = p.gt.d_base;
+  j.off = p.gt.d_chan_off;
+  j.task = p.gt.d_task;
+  j.ent_a = p.gt.d_ent_a;
+  j.ent_w = p.gt.d_ent_w;
+  j.dscale = reinterpret_cast<const float4*>(p.d_dscale);
+  j.part = part;
+  j.part_auto = part_auto;
+  j.status = p.d_status;
+  j.W = ws.W;
+  j.units = ws.units;
+  j.T = T;
+  j.C = p.C;
+  j.A = p.A;
+  j.spans = ws.spans;
+  j.q128 = p.N == 128 ? 1 : 0;
+  j.ent_in_smem = p.ent_in_smem;
+  j.first_item = 0;
+  j.n_items = ws.ctas;
+  return j;
+}
+
 template <int XF>
 cudaError_t dft_launch(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
-                       int* part_auto, cudaStream_t s) {
-  auto kern = p.N == 128 ? dft_image_kernel<XF, true> : dft_image_kernel<XF, false>;
-  kern<<<ws.ctas, kThreads, p.smem, s>>>(d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, p.d_coef, p.gt.d_cnt,
-                                         p.gt.d_base, p.gt.d_chan_off, p.gt.d_task, p.gt.d_ent_a, p.gt.d_ent_w,
-                                         p.gt.max_chan_entries, p.ent_in_smem,
-                                         reinterpret_cast<const uint32_t*>(p.d_fmat), p.d_twiddle, part, part_auto,
-                                         p.d_status);
+                       int* part_auto, cudaStream_t s, unsigned long long test_wait_ns) {
+  const DftJob job = job_of(p, d_volts, T, ws, part, part_auto);
+  const DftQueue none{nullptr, 0, 0, 0, nullptr};
+  auto kern = p.N == 128 ? dft_image_kernel<XF, true, false> : dft_image_kernel<XF, false, false>;
+  kern<<<ws.ctas, kThreads, p.smem, s>>>(job, none, p.A, p.ent_in_smem ? p.gt.max_chan_entries : 0,
+                                         reinterpret_cast<const uint32_t*>(p.d_fmat), p.d_twiddle, test_wait_ns);
+  return cudaGetLastError();
+}
+
+template <int XF>
+cudaError_t dft_batch_launch(const DftQueue& q, int A_lay, int max_entries, const uint32_t* fmat,
+                             const float2* twiddle, int ctas, size_t smem, cudaStream_t s) {
+  const DftJob none{};
+  dft_image_kernel<XF, false, true><<<ctas, kThreads, smem, s>>>(none, q, A_lay, max_entries, fmat, twiddle, 0ull);
   return cudaGetLastError();
 }
 
 template <int XF>
 cudaError_t dft_attr() {
-  cudaError_t e = allow_max_smem(dft_image_kernel<XF, false>);
-  if (e == cudaSuccess) e = allow_max_smem(dft_image_kernel<XF, true>);
+  cudaError_t e = allow_max_smem(dft_image_kernel<XF, false, false>);
+  if (e == cudaSuccess) e = allow_max_smem(dft_image_kernel<XF, true, false>);
+  if (e == cudaSuccess) e = allow_max_smem(dft_image_kernel<XF, false, true>);
   return e;
 }
 
@@ -652,10 +896,13 @@ cudaError_t dft_attr() {
 size_t dft_smem_need(int A, int max_entries) { return dft_smem_bytes(A, max_entries); }
 
 cudaError_t launch_dft_tables(Plan& p, cudaStream_t s) {
-  if (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_BF16)
+  if (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_BF16) {
     dft_matrix_kernel<true><<<128, 128, 0, s>>>(p.d_fmat);
-  else
+  } else {
     dft_matrix_kernel<false><<<128, 128, 0, s>>>(p.d_fmat);
+    dft_scale_kernel<<<p.C, kN, 0, s>>>(p.A, p.P, p.N, p.S, p.vq, p.d_csr_ptr, p.d_csr_ent, p.d_coef64,
+                                        reinterpret_cast<float4*>(p.d_dscale));
+  }
   return cudaGetLastError();
 }
 
@@ -681,13 +928,32 @@ cudaError_t dft_image_config(Plan& p, int* ctas_per_sm) {
   return cudaSuccess;
 }
 
+size_t dft_batch_smem(int A_lay, int max_entries) { return dft_smem_bytes(A_lay, max_entries); }
+
+cudaError_t launch_dft_batch(int xform, const DftQueue& q, int A_lay, int max_entries, const uint16_t* fmat,
+                             const float2* twiddle, int ctas, cudaStream_t s) {
+  const size_t smem = dft_smem_bytes(A_lay, max_entries);
+  const uint32_t* f = reinterpret_cast<const uint32_t*>(fmat);
+  switch (xform) {
+    case EPIC_XFORM_DFT_BF16X3: return dft_batch_launch<EPIC_XFORM_DFT_BF16X3>(q, A_lay, max_entries, f, twiddle, ctas, smem, s);
+    case EPIC_XFORM_DFT_FP16X3: return dft_batch_launch<EPIC_XFORM_DFT_FP16X3>(q, A_lay, max_entries, f, twiddle, ctas, smem, s);
+    case EPIC_XFORM_DFT_BF16: return dft_batch_launch<EPIC_XFORM_DFT_BF16>(q, A_lay, max_entries, f, twiddle, ctas, smem, s);
+    default: return dft_batch_launch<EPIC_XFORM_DFT_FP16>(q, A_lay, max_entries, f, twiddle, ctas, smem, s);
+  }
+}
+
+DftJob dft_job(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part, int* part_auto) {
+  return job_of(p, d_volts, T, ws, part, part_auto);
+}
+
 cudaError_t launch_dft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
-                             int* part_auto, cudaStream_t s) {
+                             int* part_auto, cudaStream_t s, unsigned long long test_wait_ns) {
+  const unsigned long long tw = test_wait_ns;
   switch (p.xform) {
-    case EPIC_XFORM_DFT_BF16X3: return dft_launch<EPIC_XFORM_DFT_BF16X3>(p, d_volts, T, ws, part, part_auto, s);
-    case EPIC_XFORM_DFT_FP16X3: return dft_launch<EPIC_XFORM_DFT_FP16X3>(p, d_volts, T, ws, part, part_auto, s);
-    case EPIC_XFORM_DFT_BF16: return dft_launch<EPIC_XFORM_DFT_BF16>(p, d_volts, T, ws, part, part_auto, s);
-    default: return dft_launch<EPIC_XFORM_DFT_FP16>(p, d_volts, T, ws, part, part_auto, s);
+    case EPIC_XFORM_DFT_BF16X3: return dft_launch<EPIC_XFORM_DFT_BF16X3>(p, d_volts, T, ws, part, part_auto, s, tw);
+    case EPIC_XFORM_DFT_FP16X3: return dft_launch<EPIC_XFORM_DFT_FP16X3>(p, d_volts, T, ws, part, part_auto, s, tw);
+    case EPIC_XFORM_DFT_BF16: return dft_launch<EPIC_XFORM_DFT_BF16>(p, d_volts, T, ws, part, part_auto, s, tw);
+    default: return dft_launch<EPIC_XFORM_DFT_FP16>(p, d_volts, T, ws, part, part_auto, s, tw);
   }
 }
 

@@ -609,6 +609,15 @@ cudaError_t launch_debug_grid(Plan& p, const uint8_t* d_volts, int T, int t, int
 // same register layouts in reverse (columns, then rows), and degrids H over each
 // antenna's kernel box.  Per-antenna sums stay in registers (thread a owns
 // antenna a) and are written per channel span, like the partial images.
+//
+// N = 32 and N = 64 grids run directly; a 128 x 128 grid folded into four
+// 64 x 64 problems (Q: virtual channel 4 c + q, output-parity subset q =
+// alpha + 2 beta) runs the adjoint of the fold as well: the forward field is
+// H_q = Tw . Fold_q(G) with Tw = exp(+2 pi i (alpha x + beta y) / 128) and
+// Fold_q(G)[y][x] = sum_{u,s} (-1)^(alpha s + beta u) G[y + 64 u][x + 64 s], so
+// the back-projected field at grid cell (y + 64 u, x + 64 s) is
+// (-1)^(alpha s + beta u) conj(Tw[y][x]) H'_q[y][x], which the degrid reads; the
+// residual of subset q is that of the output pixels (2 j + beta, 2 i + alpha).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -616,9 +625,9 @@ struct AdjSmem {
   size_t R, scr, wst, coef, dph, E, resid, box, wts, ent_a, ent_w, total;
 };
 
-template <int P>
+template <int N, int P>
 __host__ __device__ inline AdjSmem adj_smem_layout(int A, int S, int max_entries, int ent_in_smem) {
-  using G = Geo<64>;
+  using G = Geo<N>;
   AdjSmem L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -626,13 +635,13 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int A, int S, int max_entries
     o += (bytes + 15) & ~(size_t)15;
     return at;
   };
-  L.R = take(sizeof(float2) * P * 64 * 64);
+  L.R = take(sizeof(float2) * P * N * N);
   L.scr = take(sizeof(float2) * (G::THREADS / 32) * G::SCR);
   L.wst = take(sizeof(int) * 2 * (G::THREADS / 32) * 8);
   L.coef = take(sizeof(float2) * A * P);
   L.dph = take(sizeof(float2) * A * P);
   L.E = take((P == 2 ? 16 : 8) * (size_t)(A + 1));
-  L.resid = take(sizeof(float) * P * 64 * 64);
+  L.resid = take(sizeof(float) * P * N * N);
   L.box = take(sizeof(int2) * A);
   L.wts = take(sizeof(float) * 2 * (size_t)A * S);
   L.ent_a = take(ent_in_smem ? sizeof(uint16_t) * (size_t)max_entries : 0);
@@ -641,8 +650,8 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int A, int S, int max_entries
   return L;
 }
 
-template <int P>
-__global__ void __launch_bounds__(512, 1)
+template <int N, int P, bool Q>
+__global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     adjoint_kernel(const uint8_t* __restrict__ volts, int T, int C, int A, int S, long long W, long long units,
                    int spans, const float2* __restrict__ coef, const double2* __restrict__ dphase,
                    const int* __restrict__ g_cnt, const int* __restrict__ g_base, const int* __restrict__ g_off,
@@ -650,10 +659,11 @@ __global__ void __launch_bounds__(512, 1)
                    int ent_in_smem, const float2* __restrict__ twiddle, const float* __restrict__ resid,
                    const int* __restrict__ box, const double* __restrict__ wx, const double* __restrict__ wy,
                    float2* __restrict__ gpart) {
-  using G = Geo<64>;
-  constexpr int N = 64, NT = 512, NN = N * N, R1 = 8, HALF = 32, WARPS = NT / 32;
+  using G = Geo<N>;
+  constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2, WARPS = NT / 32;
+  constexpr int NG = Q ? 2 * N : N;  // side of the plan's grid (and residual)
   extern __shared__ __align__(16) unsigned char smem[];
-  const AdjSmem L = adj_smem_layout<P>(A, S, max_entries, ent_in_smem);
+  const AdjSmem L = adj_smem_layout<N, P>(A, S, max_entries, ent_in_smem);
   float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
   float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
   int* cnt_s = reinterpret_cast<int*>(smem + L.wst);
@@ -674,7 +684,7 @@ __global__ void __launch_bounds__(512, 1)
   float2 tw[8];
   tw[0] = make_float2(1.f, 0.f);
 #pragma unroll
-  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[(n1 * k2) & (N - 1)];
+  for (int k2 = 1; k2 < 8; ++k2) tw[k2] = twiddle[Q ? ((n1 * k2) & (N - 1)) * 2 : (n1 * k2) & (N - 1)];
 
   const long long u0 = (long long)blockIdx.x * W;
   const long long u1 = min(u0 + W, units);
@@ -698,6 +708,7 @@ __global__ void __launch_bounds__(512, 1)
 
   for (long long u = u0; u < u1; ++u) {
     const int c = (int)(u / T), t = (int)(u % T);
+    const int cr = Q ? c >> 2 : c;  // the plan's channel (c is a virtual channel when folded)
     if (c != cur_c) {
       if (cur_c >= 0) {
         flush(cur_c);
@@ -711,16 +722,22 @@ __global__ void __launch_bounds__(512, 1)
         base_s[tid] = g_base[(size_t)c * WARPS * 8 + tid];
       }
       for (int k = tid; k < A * P; k += NT) {
-        coef_s[k] = coef[(size_t)c * A * P + k];
-        const double2 d = dphase[(size_t)c * A * P + k];
+        coef_s[k] = coef[(size_t)cr * A * P + k];
+        const double2 d = dphase[(size_t)cr * A * P + k];
         dph_s[k] = make_float2((float)d.x, (float)d.y);
       }
-      for (int k = tid; k < P * NN; k += NT) res_s[k] = resid[(size_t)c * 2 * NN + k];
+      // the residual of the pixels this (virtual) channel images
+      for (int k = tid; k < P * NN; k += NT) {
+        const int p = k / NN, j = (k % NN) / N, i = k % N;
+        const int al = Q ? (c & 1) : 0, be = Q ? ((c >> 1) & 1) : 0;
+        res_s[k] = Q ? resid[((size_t)cr * 2 + p) * NG * NG + (size_t)(2 * j + be) * NG + 2 * i + al]
+                     : resid[(size_t)c * 2 * NN + k];
+      }
       for (int a = tid; a < A; a += NT) {
-        box_s[a] = make_int2(box[((size_t)c * A + a) * 2], box[((size_t)c * A + a) * 2 + 1]);
+        box_s[a] = make_int2(box[((size_t)cr * A + a) * 2], box[((size_t)cr * A + a) * 2 + 1]);
         for (int k = 0; k < S; ++k) {
-          wx_s[a * S + k] = (float)wx[((size_t)c * A + a) * S + k];
-          wy_s[a * S + k] = (float)wy[((size_t)c * A + a) * S + k];
+          wx_s[a * S + k] = (float)wx[((size_t)cr * A + a) * S + k];
+          wy_s[a * S + k] = (float)wy[((size_t)cr * A + a) * S + k];
         }
       }
       const int e0 = g_off[c], ne = g_off[c + 1] - e0;
@@ -741,7 +758,7 @@ __global__ void __launch_bounds__(512, 1)
     // 1. unpack and calibrate with the call's coefficients (thread a = tid)
     unsigned raw = 0;
     if (tid < A) {
-      const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
+      const uint8_t* base = volts + ((size_t)t * C + cr) * (size_t)A * P;
       if constexpr (P == 2)
         raw = __ldg(reinterpret_cast<const unsigned short*>(base) + tid);
       else
@@ -783,6 +800,12 @@ __global__ void __launch_bounds__(512, 1)
             gx.y = fmaf(w1, e1.y, fmaf(w0, e0.y, gx.y));
           }
         }
+        if constexpr (Q) {
+          // H_q = exp(+2 pi i (alpha x + beta y) / 128) x the folded gather, as in fft_image_kernel
+          const float2 w = __ldg(twiddle + (((cur_c & 1) * (n1 + R1 * n2) + ((cur_c >> 1) & 1) * y) & 127));
+          gx = make_float2(gx.x * w.x - gx.y * w.y, gx.x * w.y + gx.y * w.x);
+          gy = make_float2(gy.x * w.x - gy.y * w.y, gy.x * w.y + gy.y * w.x);
+        }
         v[0][n2] = gx;
         if constexpr (P == 2) v[1][n2] = gy;
       }
@@ -817,7 +840,24 @@ __global__ void __launch_bounds__(512, 1)
           const float rr = res_s[(size_t)p * NN + row * N + col];
           v[s] = make_float2(rr * v[s].x, -rr * v[s].y);  // conj(R Y)
         }
-        fft_line<N>(v, tw, scr, r, n1);  // element index n1 + 8 s: the input layout again
+        if constexpr (N != 64) {
+          // at N = 32 a thread's outputs (rows kidx(n1, s)) are not the elements
+          // n1 + R1 s the next transform takes: pass the column through shared
+          // memory (its R1 threads are lanes of one warp, the only ones using it)
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int y = G::kidx(n1, s);
+            Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))] = v[s];
+          }
+          __syncwarp();
+#pragma unroll
+          for (int m2 = 0; m2 < 8; ++m2) {
+            const int y = n1 + R1 * m2;
+            v[m2] = Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))];
+          }
+          __syncwarp();
+        }
+        fft_line<N>(v, tw, scr, r, n1);  // at N = 64 element index n1 + 8 s: the input layout again
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
           const int y = G::kidx(n1, s);
@@ -835,8 +875,9 @@ __global__ void __launch_bounds__(512, 1)
       for (int p = 0; p < P; ++p) {
         float2 v[8];
         float2* Rrow = Rbuf + (size_t)p * NN + y * N;
+        // element n1 + R1 n2 of the row (at N = 64 the same position as rowpos(n1, n2))
 #pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rrow[G::rowpos(n1, n2, sw)];
+        for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rrow[(n1 + R1 * n2) ^ sw];
         fft_line<N>(v, tw, scr, r, n1);
 #pragma unroll
         for (int s = 0; s < 8; ++s) Rrow[G::rowpos(n1, s, sw)] = make_float2(v[s].x, -v[s].y);
@@ -851,15 +892,25 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
       for (int p = 0; p < P; ++p) D[p] = make_float2(0.f, 0.f);
       for (int dy = 0; dy < S; ++dy) {
-        const int y = bx.y + dy;
+        const int yg = bx.y + dy, y = yg & (N - 1);  // grid row, and its row of the folded field
         const float wyv = wy_s[tid * S + dy];
         const int sw = G::swz(y);
         for (int dx = 0; dx < S; ++dx) {
-          const float w = wyv * wx_s[tid * S + dx];
-          const int idx = y * N + ((bx.x + dx) ^ sw);
+          const int xg = bx.x + dx, x = xg & (N - 1);
+          float w = wyv * wx_s[tid * S + dx];
+          float2 tc = make_float2(1.f, 0.f);
+          if constexpr (Q) {
+            // the fold's adjoint: sign (-1)^(alpha s + beta u), conj(Tw[y][x])
+            const int al = cur_c & 1, be = (cur_c >> 1) & 1;
+            if ((al & (xg >> 6)) ^ (be & (yg >> 6))) w = -w;
+            const float2 tw128 = __ldg(twiddle + ((al * x + be * y) & 127));
+            tc = make_float2(tw128.x, -tw128.y);
+          }
+          const int idx = y * N + (x ^ sw);
 #pragma unroll
           for (int p = 0; p < P; ++p) {
-            const float2 h = Rbuf[(size_t)p * NN + idx];
+            float2 h = Rbuf[(size_t)p * NN + idx];
+            if constexpr (Q) h = make_float2(h.x * tc.x - h.y * tc.y, h.x * tc.y + h.y * tc.x);
             D[p].x = fmaf(w, h.x, D[p].x);
             D[p].y = fmaf(w, h.y, D[p].y);
           }
@@ -888,8 +939,23 @@ cudaError_t launch_fft_image_coef(Plan& p, const uint8_t* d_volts, int T, const 
 
 namespace {
 size_t adj_smem(const Plan& p, int ent) {
-  return p.P == 2 ? adj_smem_layout<2>(p.A, p.S, p.gt.max_chan_entries, ent).total
-                  : adj_smem_layout<1>(p.A, p.S, p.gt.max_chan_entries, ent).total;
+  const int me = p.gt.max_chan_entries;
+  if (p.N == 32)
+    return p.P == 2 ? adj_smem_layout<32, 2>(p.A, p.S, me, ent).total : adj_smem_layout<32, 1>(p.A, p.S, me, ent).total;
+  return p.P == 2 ? adj_smem_layout<64, 2>(p.A, p.S, me, ent).total : adj_smem_layout<64, 1>(p.A, p.S, me, ent).total;
+}
+
+template <int N, int P, bool Q>
+cudaError_t adjoint_launch(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, int ent, size_t smem,
+                           cudaStream_t s) {
+  auto fn = adjoint_kernel<N, P, Q>;
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  fn<<<ws.ctas, Geo<N>::THREADS, smem, s>>>(d_volts, T, p.C, p.A, p.S, ws.W, ws.units, ws.spans, p.d_gcoef,
+                                            p.d_dphase, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off, p.gt.d_ent_a,
+                                            p.gt.d_ent_w, p.gt.max_chan_entries, ent, p.d_twiddle, p.d_resid,
+                                            p.d_box, p.d_wx, p.d_wy, p.d_gpart);
+  return cudaGetLastError();
 }
 }  // namespace
 
@@ -899,15 +965,18 @@ cudaError_t launch_adjoint(Plan& p, const uint8_t* d_volts, int T, const WorkSpl
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int ent = adj_smem(p, 1) <= (size_t)optin ? 1 : 0;
   const size_t smem = adj_smem(p, ent);
-  auto fn = p.P == 2 ? adjoint_kernel<2> : adjoint_kernel<1>;
-  cudaError_t e = allow_max_smem(fn);
-  if (e != cudaSuccess) return e;
-  fn<<<ws.ctas, 512, smem, s>>>(d_volts, T, p.C, p.A, p.S, ws.W, ws.units, ws.spans, p.d_gcoef, p.d_dphase,
-                                 p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off, p.gt.d_ent_a, p.gt.d_ent_w,
-                                 p.gt.max_chan_entries, ent, p.d_twiddle, p.d_resid, p.d_box, p.d_wx, p.d_wy,
-                                 p.d_gpart);
-  return cudaGetLastError();
+  if (p.N == 32)
+    return p.P == 2 ? adjoint_launch<32, 2, false>(p, d_volts, T, ws, ent, smem, s)
+                    : adjoint_launch<32, 1, false>(p, d_volts, T, ws, ent, smem, s);
+  if (p.N == 128)  // folded into four 64 x 64 problems
+    return p.P == 2 ? adjoint_launch<64, 2, true>(p, d_volts, T, ws, ent, smem, s)
+                    : adjoint_launch<64, 1, true>(p, d_volts, T, ws, ent, smem, s);
+  return p.P == 2 ? adjoint_launch<64, 2, false>(p, d_volts, T, ws, ent, smem, s)
+                  : adjoint_launch<64, 1, false>(p, d_volts, T, ws, ent, smem, s);
 }
+
+// Antennas an adjoint launch handles: one per thread.
+int adjoint_max_ant(int N) { return N == 32 ? Geo<32>::THREADS : Geo<64>::THREADS; }
 
 size_t adjoint_smem_need(const Plan& p) { return adj_smem(p, 0); }
 

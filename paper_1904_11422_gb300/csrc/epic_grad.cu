@@ -67,7 +67,7 @@ __global__ void loss_sum_kernel(int C, const double* __restrict__ loss_part, flo
 // the warp adds |FT w_y(j)| x row in FP64.
 constexpr int kGradAntPerBlock = 8;
 __global__ void __launch_bounds__(32 * kGradAntPerBlock)
-    grad_reduce_kernel(int T, int A, int P, int N, long long W, int ctas, int spans, int subtract,
+    grad_reduce_kernel(int T, int A, int P, int N, int vq, long long W, int ctas, int spans, int subtract,
                        const float2* __restrict__ gpart, const int* __restrict__ part_auto,
                        const float* __restrict__ resid, const float* __restrict__ kx2,
                        const float* __restrict__ ky2, const float* __restrict__ gains,
@@ -83,22 +83,29 @@ __global__ void __launch_bounds__(32 * kGradAntPerBlock)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = blockIdx.y * kGradAntPerBlock + warp;
   if (a >= A) return;
-  const long long b_lo = ((long long)c * T) / W;
-  const long long b_hi = min(((long long)(c + 1) * T - 1) / W, (long long)ctas - 1);
+  // data term: the CTA sums of every (virtual) channel of c, in order; self
+  // powers from the first (each virtual channel of a folded grid holds them all)
   double dr[2] = {0.0, 0.0}, di[2] = {0.0, 0.0};
   long long pw[2] = {0, 0};
-  for (long long b = b_lo; b <= b_hi; ++b) {
-    const int slot = c - (int)((b * W) / T);
+  for (int q = 0; q < vq; ++q) {
+    const int cv = c * vq + q;
+    const long long b_lo = ((long long)cv * T) / W;
+    const long long b_hi = min(((long long)(cv + 1) * T - 1) / W, (long long)ctas - 1);
+    for (long long b = b_lo; b <= b_hi; ++b) {
+      const int slot = cv - (int)((b * W) / T);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      if (p >= P) break;
-      const float2 v = gpart[((size_t)(b * spans + slot) * A + a) * P + p];
-      dr[p] += v.x;
-      di[p] += v.y;
+      for (int p = 0; p < 2; ++p) {
+        if (p >= P) break;
+        const float2 v = gpart[((size_t)(b * spans + slot) * A + a) * P + p];
+        dr[p] += v.x;
+        di[p] += v.y;
+      }
+      if (q == 0) {
+        const int4 qa = reinterpret_cast<const int4*>(part_auto)[(b * spans + slot) * A + a];
+        pw[0] += qa.x;
+        pw[1] += qa.y;
+      }
     }
-    const int4 q = reinterpret_cast<const int4*>(part_auto)[(b * spans + slot) * A + a];
-    pw[0] += q.x;
-    pw[1] += q.y;
   }
   const float* kx = kx2 + ((size_t)c * A + a) * N;
   const float* ky = ky2 + ((size_t)c * A + a) * N;
@@ -153,7 +160,7 @@ cudaError_t launch_grad_reduce(Plan& p, int T, const WorkSplit& ws, const float*
     if (e != cudaSuccess) return e;
   }
   dim3 grid(p.C, (p.A + kGradAntPerBlock - 1) / kGradAntPerBlock);
-  grad_reduce_kernel<<<grid, 32 * kGradAntPerBlock, smem, s>>>(T, p.A, p.P, p.N, ws.W, ws.ctas, ws.spans,
+  grad_reduce_kernel<<<grid, 32 * kGradAntPerBlock, smem, s>>>(T, p.A, p.P, p.N, p.vq, ws.W, ws.ctas, ws.spans,
                                                                p.subtract, p.d_gpart, p.d_part_auto, p.d_resid,
                                                                p.d_kx2, p.d_ky2, d_gains, d_grad);
   return cudaGetLastError();

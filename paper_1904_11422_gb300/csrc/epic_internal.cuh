@@ -38,6 +38,16 @@ struct WorkSplit {
   int spans;       // partial-image slots per CTA used by this call (ctas * spans fits the workspace)
 };
 
+// The split of an imaging call: units u = c*T + t (channel-major) in equal
+// contiguous ranges, one per CTA (at most `cap` CTAs, or the plan's own cap),
+// no CTA left empty; spans = the most channels any CTA touches.  split_fits
+// says whether the split's (CTA, span) slots fit the plan's workspace.
+int spans_needed(const WorkSplit& ws);
+struct Plan;
+WorkSplit split_work_cap(const Plan& p, int T, int cap);
+WorkSplit split_work(const Plan& p, int T);
+bool split_fits(const Plan& p, const WorkSplit& ws);
+
 // Gather tables of a gridder (see epic_gather.cu).
 enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutPair64 = 3, kLayoutFft128 = 4,
              kLayoutPairQ = 5, kLayoutPairD = 6, kLayoutFft64Q = 7 };
@@ -81,6 +91,7 @@ struct Plan {
   int2* d_csr_ent = nullptr;    // [C][A*S*S] (antenna, weight bits), antenna order
   float2* d_twiddle = nullptr;  // [N] exp(+2 pi i m / N)
   uint16_t* d_fmat = nullptr;   // tensor path: real DFT matrix, hi/lo 16-bit, shared-memory image (64 KB)
+  float* d_dscale = nullptr;    // FP16 tensor path: [C * vq][4] power-of-two scales (fields, stage 1, squares)
   int* d_status = nullptr;      // device error word
   GatherTables gt;              // gridder's lane-interleaved gather tables
 
@@ -105,7 +116,8 @@ struct Plan {
   std::vector<long long> kind_launches;
   std::vector<double> kind_ms;
 
-  // epic_grad workspace (FP32 FFT plans with N = 64 and A <= 512)
+  // epic_grad workspace (FP32 plans of the fft_image kernel: N = 32 with A <= 128,
+  // N = 64 and folded N = 128 with A <= 512)
   bool grad_ok = false;
   float2* d_gcoef = nullptr;     // [C][A][P] coefficients g * delay phase of the call
   double2* d_gcoef64 = nullptr;  // [C][A][P] the same in FP64
@@ -161,12 +173,73 @@ cudaError_t fft128_config(Plan& p, int* clusters);
 cudaError_t launch_fft128_image_ws(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
                                    int* part_auto, cudaStream_t s);
 
+// What one block-end reduction needs of a plan and of its call's split.
+struct ReduceArgs {
+  int T, C, A, N, vq, dec, ctas, spans, subtract, accumulate;
+  long long W;
+  const float* part;
+  const int* part_auto;
+  const double2* coef64;
+  const float* kx2;
+  const float* ky2;
+  float* out;
+};
+
+// One imaging problem of the tensor-core kernel: a plan's tables and the split
+// of one call over its units (CTA-sized spans of W units, each span an "item").
+struct DftJob {
+  const uint8_t* volts;
+  const float2* coef;
+  const int* cnt;
+  const int* base;
+  const int* off;
+  const uint16_t* task;
+  const uint16_t* ent_a;
+  const float* ent_w;
+  const float4* dscale;
+  float* part;
+  int* part_auto;
+  int* status;
+  long long W, units;
+  int T, C, A, spans, q128, ent_in_smem;
+  int first_item, n_items;  // a batch's items [first_item, first_item + n_items) are this job's spans
+  // batch only: the job's block-end reduction, run in the same launch as items
+  // [red_first, red_first + n_red) of the queue (numbered after every imaging
+  // item), each `red_rows` rows of one virtual channel; done[cv] counts
+  // the imaging items that have written their partial image of virtual channel cv
+  ReduceArgs red;
+  int* done;
+  int red_first, n_red, red_rows;
+};
+// A batch's work list: the items of several jobs (jobs ordered by first_item),
+// claimed one at a time by the CTAs of one persistent launch.
+struct DftQueue {
+  const DftJob* jobs;
+  int n_jobs, n_items;  // all items: imaging items first, then reduction items
+  int n_image_items;
+  int* head;  // the next unclaimed item; zero when the launch starts
+};
+
+// Pixels of one row per thread in the reduction items of a batch launch.
+constexpr int kBatchReducePix = 2;
+// The job of one call of a tensor-core plan (its first_item is 0).
+DftJob dft_job(const Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part, int* part_auto);
+// Shared memory of a persistent batch launch whose jobs have at most A_lay
+// antennas and max_entries gather entries held in shared memory.
+size_t dft_batch_smem(int A_lay, int max_entries);
+// One persistent launch of `ctas` CTAs that image every item of q (device
+// memory: q.jobs, q.head, which must be 0); all jobs share the transform xform.
+cudaError_t launch_dft_batch(int xform, const DftQueue& q, int A_lay, int max_entries, const uint16_t* fmat,
+                             const float2* twiddle, int ctas, cudaStream_t s);
+
 // Tensor-core path (DFT-by-GEMM on tcgen05; N = 64, two polarisations).
 size_t dft_smem_need(int A, int max_entries);
 cudaError_t launch_dft_tables(Plan& p, cudaStream_t s);
 cudaError_t dft_image_config(Plan& p, int* ctas_per_sm);
+// test_wait_ns > 0: the first mbarrier wait of every CTA waits on a barrier
+// that nothing arrives at, for that long, and takes the time-out path (tests).
 cudaError_t launch_dft_image(Plan& p, const uint8_t* d_volts, int T, const WorkSplit& ws, float* part,
-                             int* part_auto, cudaStream_t s);
+                             int* part_auto, cudaStream_t s, unsigned long long test_wait_ns = 0);
 
 // Gradient of the image-plane loss (epic_grad), FP32 FFT path at N = 64.
 cudaError_t launch_grad_coef(Plan& p, const float* d_gains, cudaStream_t s);
@@ -179,6 +252,7 @@ cudaError_t launch_adjoint(Plan& p, const uint8_t* d_volts, int T, const WorkSpl
 cudaError_t launch_grad_reduce(Plan& p, int T, const WorkSplit& ws, const float* d_gains, float* d_grad,
                                cudaStream_t s);
 size_t adjoint_smem_need(const Plan& p);
+int adjoint_max_ant(int N);
 
 // Block end: sum the CTA partials of every channel in a fixed order, remove the
 // autocorrelation term, write or accumulate the output.

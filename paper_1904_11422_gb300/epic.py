@@ -92,6 +92,7 @@ SIGNATURES = {
     "epic_debug_transform": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
     "epic_debug_check_plan": (_I, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "epic_debug_fma_rate": (_I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
+    "epic_debug_image_timeout": (_I, [_P, _P, _I, ctypes.c_longlong, _P]),
     "epic_image_host_async": (_I, [_P, _P, _I, _P, _I, _P]),
     "epic_timing_enable": (_I, [_P, _I]),
     "epic_timing_read": (_I, [_P, ctypes.POINTER(epic_kernel_time), _I, ctypes.POINTER(_I)]),
@@ -417,6 +418,14 @@ def epic_debug_transform(plan: Plan, d_volts, n_time: int, t: int, c: int, p: in
     _check_size(d_y, 8 * plan.info["grid_n"] ** 2, "d_y")
     _check(load_library().epic_debug_transform(plan.handle, _ptr(d_volts), int(n_time), int(t), int(c), int(p),
                                                _ptr(d_y), _stream(stream)), "epic_debug_transform")
+
+
+def epic_debug_image_timeout(plan: Plan, d_volts, n_time: int, wait_ns: int, stream=None) -> None:
+    """Tensor-core imaging whose first bounded wait per CTA cannot succeed (see
+    include/epic.h); the next epic_sync raises EpicError(EPIC_ERR_TIMEOUT)."""
+    _check_size(d_volts, plan.volts_bytes(n_time), "d_volts")
+    _check(load_library().epic_debug_image_timeout(plan.handle, _ptr(d_volts), int(n_time), int(wait_ns),
+                                                   _stream(stream)), "epic_debug_image_timeout")
 
 
 def epic_debug_check_plan(plan: Plan) -> str:

@@ -23,6 +23,33 @@ def channel_shard(n_chan: int, rank: int, world: int) -> tuple[int, int]:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def rank_channels(n_chan: int, rank: int, world: int, mode: str) -> tuple[int, int]:
+    """[c_lo, c_hi) of the band a rank images in a multi-GPU run.
+
+    mode "replicate": every rank images the whole band of its own block (weak
+    scaling: per-GPU work fixed as ranks are added); mode "channels": the ranks
+    split one block's band into contiguous balanced ranges (strong scaling: the
+    paper's per-GPU bandwidth split, Sec. 5.1)."""
+    if mode == "replicate":
+        if world < 1 or not 0 <= rank < world:
+            raise ValueError("bad shard request")
+        return 0, n_chan
+    if mode == "channels":
+        return channel_shard(n_chan, rank, world)
+    raise ValueError(f"unknown shard mode {mode!r}")
+
+
+def job_units(block_units: int, world: int, mode: str) -> int:
+    """Antenna x channel x sample units the whole job images per step: one block
+    per rank when replicating, one block split over the ranks otherwise."""
+    return block_units * world if mode == "replicate" else block_units
+
+
+def scaling(mode: str) -> str:
+    """The bench line's "scaling" key for a shard mode."""
+    return "weak" if mode == "replicate" else "strong"
+
+
 def time_shard(n_time: int, rank: int, world: int) -> tuple[int, int]:
     """[t_lo, t_hi) of rank's samples of a block: contiguous, sizes differing by at most 1."""
     return channel_shard(n_time, rank, world)

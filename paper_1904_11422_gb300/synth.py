@@ -210,6 +210,39 @@ def random_small(seed: int, n_ant: int = 6, n_pol: int = 2, n_chan: int = 2, gri
                     gains=gains, delays_s=delays)
 
 
+def channel_slice(w: Workload, lo: int, hi: int) -> Workload:
+    """The channels [lo, hi) of a workload (voltages, frequencies, gains), as
+    one rank of a channel-split run holds them."""
+    import copy
+    out = copy.copy(w)
+    out.name = f"{w.name}[{lo}:{hi}]"
+    out.freq_hz = np.ascontiguousarray(w.freq_hz[lo:hi])
+    out.volts = np.ascontiguousarray(w.volts[:, lo:hi])
+    out.gains = None if w.gains is None else np.ascontiguousarray(w.gains[lo:hi])
+    return out
+
+
+def saturated_plane_wave(seed: int, n_ant: int = 1024, grid_n: int = 64, n_chan: int = 2, n_time: int = 3,
+                         support: int = 5, gain_amp: float = 16.0) -> Workload:
+    """The largest fields a block can hold: one noise-free plane wave from a
+    pixel centre near the zenith, at the 4-bit limit on every antenna (amplitude
+    7 per component before quantisation, so most samples saturate), both
+    polarisations, with gains of modulus gain_amp and random phases.  Antennas
+    uniform in the largest disk whose boxes stay inside the grid."""
+    rng = np.random.default_rng(seed)
+    freq = np.linspace(60e6, 76e6, n_chan)
+    lam_min = C_LIGHT / freq.max()
+    ant = disk_positions(n_ant, 0.5 * lam_min * (grid_n - support - 3), 0.0, seed + 1)
+    i, j = grid_n // 2 + 2, grid_n // 2 - 1
+    l, m = pixel_direction(grid_n, 0.5, i, j)
+    ph = geometric_phase(ant, freq, l, m)  # [C][A]
+    s = np.exp(2j * np.pi * rng.random((n_time, n_chan)))
+    z = 7.0 * np.sqrt(2.0) * s[:, :, None, None] * ph[None, :, :, None] * np.ones((1, 1, 1, 2))
+    gains = gain_amp * np.exp(2j * np.pi * rng.random((n_chan, n_ant, 2)))
+    return Workload(f"saturated{seed}", ant, freq, 2, grid_n, support, 0.5, max(support - 1, 1) / 4.0,
+                    quantize4(z), gains=gains, sources=[(i, j, 7.0)])
+
+
 def differentiation(config_index: int = 4, n_chan: int = 64, n_time: int = 1250, n_sources: int = 5,
                     noise_sigma: float = 2.5):
     """Gain calibration on the station block: the station array, complex gains

@@ -8,11 +8,10 @@ import pytest
 
 from paper_1904_11422_gb300 import build_lib, epic, synth
 
-from _helpers import TOL_FP32, assert_close, gpu_image, oracle_image, rel_errors
+from _helpers import TOL, TOL_FP32, assert_close, gpu_image, oracle_image, rel_errors
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fft_fp32": TOL_FP32, "dft_bf16x3": 1e-3, "dft_fp16": 5e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -286,3 +285,47 @@ def test_plans_release_their_device_memory():
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
     assert free0 - free1 < 8 * 1024 * 1024, (free0, free1)
+
+
+# ------------------------------------------------ failure detection: bounded waits
+@pytest.mark.parametrize("xf,grid_n", [("dft_bf16x3", 64), ("dft_fp16", 128)])
+def test_tensor_kernel_wait_times_out_and_the_plan_recovers(xf, grid_n):
+    """The tensor kernel's first mbarrier wait in every CTA is made on a barrier
+    that nothing arrives at, limited to 2 ms: every CTA must give up, report
+    EPIC_ERR_TIMEOUT through epic_sync, drain the products it issued and free its
+    tensor memory, leaving the plan and the device usable (the next calls, on the
+    same plan and on a fresh one, match the oracle)."""
+    import time
+
+    import torch
+    w = synth.random_small(2301, n_ant=30, n_pol=2, n_chan=3, grid_n=grid_n, support=3, n_time=6)
+    plan = epic.plan_for(w, epic.XFORMS[xf])
+    dv = torch.from_numpy(w.volts).cuda()
+    t0 = time.time()
+    epic.epic_debug_image_timeout(plan, dv, w.n_time, 2_000_000)
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_sync(plan)
+    assert ei.value.status == epic.EPIC_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    epic.epic_sync(plan)  # the status was cleared
+    ref = oracle_image(w)
+    assert rel_errors(gpu_image(w, xform=epic.XFORMS[xf], plan=plan), ref, 2).max() <= TOL[xf]
+    plan.close()
+    assert rel_errors(gpu_image(w, xform=epic.XFORMS[xf]), ref, 2).max() <= TOL[xf]
+
+
+def test_timeout_hook_rejects_fp32_plans_and_bad_limits():
+    import torch
+    w = synth.random_small(2302, n_ant=8, n_pol=2, n_chan=1, grid_n=64, support=3, n_time=2)
+    plan = epic.plan_for(w)
+    dv = torch.from_numpy(w.volts).cuda()
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_debug_image_timeout(plan, dv, w.n_time, 2_000_000)
+    assert ei.value.status == epic.EPIC_ERR_UNSUPPORTED
+    plan.close()
+    plan = epic.plan_for(w, epic.XFORMS["dft_bf16x3"])
+    for bad in (0, 999, 2_000_000_000):
+        with pytest.raises(epic.EpicError) as ei:
+            epic.epic_debug_image_timeout(plan, dv, w.n_time, bad)
+        assert ei.value.status == epic.EPIC_ERR_INVALID_ARG
+    plan.close()

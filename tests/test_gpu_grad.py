@@ -38,6 +38,12 @@ CASES = [
     dict(seed=1302, n_ant=9, n_pol=1, n_chan=3, grid_n=64, support=5, n_time=5),
     # more antennas than half the block: one thread per antenna in the degrid
     dict(seed=1306, n_ant=300, n_pol=2, n_chan=1, grid_n=64, support=3, n_time=3),
+    # 32 x 32 grids (128-thread blocks, up to 128 antennas)
+    dict(seed=1307, n_ant=20, n_pol=2, n_chan=2, grid_n=32, support=3, n_time=5),
+    dict(seed=1308, n_ant=120, n_pol=1, n_chan=1, grid_n=32, support=5, n_time=3),
+    # 128 x 128 grids folded into four 64 x 64 problems: the fold's adjoint
+    dict(seed=1309, n_ant=24, n_pol=2, n_chan=2, grid_n=128, support=5, n_time=4),
+    dict(seed=1310, n_ant=60, n_pol=1, n_chan=1, grid_n=128, support=3, n_time=3),
 ]
 
 
@@ -54,8 +60,12 @@ def test_gradient_matches_fx_oracle(case):
     assert err <= 1e-3, err
 
 
-def test_gradient_matches_finite_differences():
-    w = synth.random_small(1303, n_ant=10, n_pol=2, n_chan=2, grid_n=64, support=5, n_time=4)
+@pytest.mark.parametrize("grid_n", [64, 32, 128])
+def test_gradient_matches_finite_differences(grid_n):
+    w = synth.random_small(1303, n_ant=10, n_pol=2, n_chan=2, grid_n=grid_n, support=5, n_time=4)
+    plan = epic.plan_for(w)
+    assert plan.info["transforms_per_image"] == (4 if grid_n == 128 else 1)
+    plan.close()
     rng = np.random.default_rng(7)
     model = rng.standard_normal((w.n_chan, 2, w.grid_n, w.grid_n)) * 20.0
     _, grad = _gpu_grad(w, w.gains, model)
@@ -136,12 +146,23 @@ def test_autograd_function():
     plan.close()
 
 
-def test_grad_unsupported_plans():
+@pytest.mark.parametrize("kind", ["tensor", "cluster128", "ants32"])
+def test_grad_unsupported_plans(kind):
+    """Tensor-core plans, 128 x 128 grids on two-CTA clusters and 32 x 32 grids
+    with more antennas than the adjoint's threads are refused."""
     import torch
-    w = synth.random_small(1305, n_ant=6, n_pol=2, n_chan=1, grid_n=32, support=3, n_time=2)
-    plan = epic.plan_for(w)
-    z = torch.zeros((1, 6, 2, 2), dtype=torch.float32, device="cuda")
-    m = torch.zeros((1, 2, 32, 32), dtype=torch.float32, device="cuda")
+    if kind == "tensor":
+        w = synth.random_small(1305, n_ant=6, n_pol=2, n_chan=1, grid_n=64, support=3, n_time=2)
+        plan = epic.plan_for(w, epic.XFORMS["dft_bf16x3"])
+    elif kind == "cluster128":
+        w = synth.random_small(1311, n_ant=450, n_pol=2, n_chan=1, grid_n=128, support=5, n_time=2)
+        plan = epic.plan_for(w)
+        assert plan.info["cluster_dim"] == 2
+    else:
+        w = synth.random_small(1312, n_ant=129, n_pol=2, n_chan=1, grid_n=32, support=3, n_time=2)
+        plan = epic.plan_for(w)
+    z = torch.zeros((1, w.n_ant, 2, 2), dtype=torch.float32, device="cuda")
+    m = torch.zeros((1, 2, w.grid_n, w.grid_n), dtype=torch.float32, device="cuda")
     with pytest.raises(epic.EpicError) as ei:
         epic.epic_grad(plan, torch.from_numpy(w.volts).cuda(), 2, z, m, torch.empty_like(z),
                        torch.empty((), device="cuda"))

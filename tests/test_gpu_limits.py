@@ -7,11 +7,10 @@ import pytest
 
 from paper_1904_11422_gb300 import build_lib, epic, synth
 
-from _helpers import TOL_FP32, gpu_image, oracle_image, rel_errors
+from _helpers import TOL, TOL_FP32, gpu_image, oracle_image, rel_errors
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fft_fp32": TOL_FP32, "dft_bf16x3": 1e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -1,20 +1,19 @@
 """Parity of the tensor-core path (DFT-by-GEMM on tcgen05) with the FP64 oracle.
 
-The compensated transforms (BF16 or FP16 hi+lo, three products, FP32
-accumulation) must stay within 1e-3 of the channel's image peak; the plain
-16-bit transforms within the bounds stated below.  Errors are measured against
-the oracle on the same seeded inputs."""
+Every transform must stay within its stated bound (tests/_helpers.TOL, relative
+to the channel's image peak): about ten times the largest error measured on
+GB300, so that a regression of the hi + lo split fails.  Errors are measured
+against the oracle on the same seeded inputs, including saturated plane waves
+whose stage-1 magnitudes exceed FP16's range unless the FP16 transforms scale
+their operands."""
 import numpy as np
 import pytest
 
 from paper_1904_11422_gb300 import build_lib, epic, synth
 
-from _helpers import gpu_image, oracle_image, rel_errors
+from _helpers import TOL, gpu_image, oracle_image, rel_errors
 
 pytestmark = pytest.mark.gpu
-
-# stated bounds, relative to the channel's image peak (station-shaped data)
-TOL = {"dft_bf16x3": 1e-3, "dft_fp16x3": 1e-3, "dft_bf16": 2e-2, "dft_fp16": 5e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,14 +54,14 @@ def test_station_block_sampled_channels(station, xf):
     ref = oracle_image(w, channels=chans, use_fft=True)
     err = rel_errors(got[chans], ref, 2)
     print(f"{xf}: max error / image peak per plane {err.max(axis=0)}")
-    assert err.max() <= TOL[xf]
+    assert err.max() <= TOL[xf], (xf, err.max())
 
 
 def test_tensor_and_fp32_paths_agree_at_full_size(station):
     w = station
     a = gpu_image(w, xform=epic.XFORMS["dft_bf16x3"])
     b = gpu_image(w, xform=epic.XFORMS["fft_fp32"])
-    assert rel_errors(a, b, 2).max() <= 1e-3
+    assert rel_errors(a, b, 2).max() <= TOL["dft_bf16x3"] + TOL["fft_fp32"]
 
 
 def test_tensor_path_deterministic_and_additive(station):
@@ -128,7 +127,7 @@ def test_grid128_station_sampled_channels(xf):
     ref = _station128_ref(chans)
     err = rel_errors(got[chans], ref, 2)
     print(f"128^2 {xf}: max error / image peak per plane {err.max(axis=0)}")
-    assert err.max() <= TOL[xf]
+    assert err.max() <= TOL[xf], (xf, err.max())
 
 
 _S128 = {}
@@ -158,3 +157,21 @@ def test_grid32_random_arrays(xf):
         for sub in (True, False):
             err = rel_errors(gpu_image(w, xform=epic.XFORMS[xf], subtract=sub), oracle_image(w, subtract=sub), 2)
             assert err.max() <= TOL[xf], (xf, seed, sub, err.max())
+
+
+# --------------------------------------- the edge of FP16's range (65 504)
+@pytest.mark.parametrize("xf", ["dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+@pytest.mark.parametrize("grid_n,gain", [(64, 16.0), (128, 16.0), (64, 4096.0), (128, 4096.0), (32, 4096.0)])
+def test_saturated_plane_wave(xf, grid_n, gain):
+    """1 024 antennas all at the 4-bit limit, one coherent source, gains of
+    modulus 16 or 4 096: with 4 096 the stage-1 result reaches ~1e6 and the
+    gridded field ~2e4, far beyond FP16's 65 504, so the FP16 transforms stay
+    finite and within bound only through their power-of-two operand scales.
+    On the 128 x 128 grid the folded fields sum four quadrants."""
+    w = synth.saturated_plane_wave(3001 + grid_n, n_ant=1024, grid_n=grid_n, gain_amp=gain)
+    got = gpu_image(w, xform=epic.XFORMS[xf])
+    assert np.isfinite(got).all()
+    ref = oracle_image(w)
+    err = rel_errors(got, ref, 2)
+    print(f"saturated plane wave N={grid_n} |g|={gain} {xf}: {err.max():.3e}")
+    assert err.max() <= TOL[xf], (xf, grid_n, gain, err.max())
