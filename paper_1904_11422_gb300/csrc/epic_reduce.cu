@@ -14,7 +14,7 @@ namespace epic {
 namespace {
 
 constexpr int kReduceThreads = 256;
-constexpr int kReducePixels = 4;     // pixels of one row per thread
+constexpr int kReducePixels = 1;     // pixels of one row per thread (more warps beat more reuse here)
 constexpr size_t kReduceSmemCap = 64 * 1024;
 
 // One block per (virtual channel, `rows` rows); the arithmetic is reduce_rows
