@@ -235,6 +235,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   float* entw_s = reinterpret_cast<float*>(abort_flag + 3);  // [max_entries]
   uint16_t* enta_s = reinterpret_cast<uint16_t*>(entw_s + max_entries);  // [max_entries]
+  // batch: the current item's job, copied from the work list (its fields are read
+  // in the per-sample code, where shared memory beats L1 under this much shared use)
+  DftJob* job_s = reinterpret_cast<DftJob*>(
+      (reinterpret_cast<uintptr_t>(enta_s + max_entries) + 15) & ~static_cast<uintptr_t>(15));
   int* claim_s = reinterpret_cast<int*>(abort_flag + 1);                  // batch: claimed item, wait result
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -439,7 +443,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       int k = 0;
       while (k + 1 < queue.n_jobs && item >= queue.jobs[k + 1].first_item) ++k;
-      jp = &queue.jobs[k];
+      {
+        const int* src = reinterpret_cast<const int*>(&queue.jobs[k]);
+        int* dst = reinterpret_cast<int*>(job_s);
+        for (int i = tid; i < (int)(sizeof(DftJob) / sizeof(int)); i += kThreads) dst[i] = src[i];
+      }
+      __syncthreads();
+      jp = job_s;
       b_item = item - jp->first_item;
       q128 = jp->q128 != 0;
     }
@@ -831,6 +841,7 @@ size_t dft_smem_bytes(int A, int max_entries) {
   b += 2 * 16 * 8 * sizeof(int);            // gather trip counts and bases
   b += 40;                                  // three mbarriers, TMEM address, abort flag
   b += 6 * (size_t)max_entries;             // gather entries (weight, antenna)
+  b += sizeof(DftJob) + 16;                 // a batch item's job
   return b + 1024;                          // alignment slack
 }
 
