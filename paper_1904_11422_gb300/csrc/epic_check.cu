@@ -164,7 +164,7 @@ extern "C" epic_status epic_debug_check_plan(const epic_plan* h, char* report, s
         const int K = cnt[slot];
         if ((int)want.size() > K) return say("set %d thread %d slot %d: %d entries, trip count %d", q, t, s, (int)want.size(), K), EPIC_ERR_INTERNAL;
         for (int k = 0; k < K; ++k) {
-          const size_t idx = (size_t)off[q] + base[slot] + 32 * (size_t)k + lane;
+          const size_t idx = (size_t)off[q] + epic::entry_pos(layout, (size_t)base[slot], k, lane);
           uint32_t wb;
           std::memcpy(&wb, &ew[idx], sizeof wb);
           if (ea[idx] >= A) return say("set %d entry %zu: antenna %d out of range", q, idx, (int)ea[idx]), EPIC_ERR_INTERNAL;

@@ -307,11 +307,16 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
       for (int n2 = 0; n2 < 8; ++n2) {
         // cell (y, n1 + R1 n2): lane-interleaved entries, warp-uniform trip count
         const int K = cnt_s[warp * 8 + n2];
-        const int b = base_s[warp * 8 + n2] + lane;
+        // a lane's entries 2j, 2j + 1 side by side (entry_pos): one 32-bit load of
+        // both antennas, one 8-byte load of both weights
+        const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (base_s[warp * 8 + n2] >> 1) + lane;
+        const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (base_s[warp * 8 + n2] >> 1) + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
         for (int k = 0; k < K; k += 2) {  // K is even: two entries per step, added in order
-          const int a0 = ent_a[b + 32 * k], a1 = ent_a[b + 32 * k + 32];
-          const float w0 = ent_w[b + 32 * k], w1 = ent_w[b + 32 * k + 32];
+          const uint32_t aa = ea2[16 * k];
+          const float2 ww = ew2[16 * k];
+          const int a0 = (int)(aa & 0xffffu), a1 = (int)(aa >> 16);
+          const float w0 = ww.x, w1 = ww.y;
           if constexpr (P == 2) {
             const float4 e0 = E4[a0], e1 = E4[a1];
             gx.x = fmaf(w1, e1.x, fmaf(w0, e0.x, gx.x));
@@ -783,11 +788,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 #pragma unroll
       for (int n2 = 0; n2 < 8; ++n2) {
         const int K = cnt_s[warp * 8 + n2];
-        const int b = base_s[warp * 8 + n2] + lane;
+        const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (base_s[warp * 8 + n2] >> 1) + lane;
+        const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (base_s[warp * 8 + n2] >> 1) + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
-        for (int k = 0; k < K; k += 2) {
-          const int a0 = ent_a[b + 32 * k], a1 = ent_a[b + 32 * k + 32];
-          const float w0 = ent_w[b + 32 * k], w1 = ent_w[b + 32 * k + 32];
+        for (int k = 0; k < K; k += 2) {  // the imaging kernel's entry pairs, in the same order
+          const uint32_t aa = ea2[16 * k];
+          const float2 ww = ew2[16 * k];
+          const int a0 = (int)(aa & 0xffffu), a1 = (int)(aa >> 16);
+          const float w0 = ww.x, w1 = ww.y;
           if constexpr (P == 2) {
             const float4 e0 = E4[a0], e1 = E4[a1];
             gx.x = fmaf(w1, e1.x, fmaf(w0, e0.x, gx.x));

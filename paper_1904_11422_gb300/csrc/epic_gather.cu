@@ -9,7 +9,9 @@
 // trip count K_ws is the largest cell count among the warp's 32 cells (rounded
 // up to even for the FFT kernel, which walks entries two at a time to keep two
 // independent load chains in flight), and entry
-// k of lane l sits at base_ws + 32 k + l, cells with fewer entries padded with
+// k of lane l sits at base_ws + 32 k + l (the FFT kernel's layouts: at
+// base_ws + 64 (k / 2) + 2 l + k % 2, a lane's two entries of a step side by side,
+// see entry_pos), cells with fewer entries padded with
 // weight-0 entries of antenna 0 (adding +0 leaves every sum unchanged, and the
 // real entries keep their antenna order, so the results are the same as a
 // per-cell loop).  Loads are coalesced and the loop has no divergence.
@@ -169,21 +171,21 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int fill, const
         const int b0 = ptr[cell], n = ptr[cell + 1] - b0;
         const bool neg = ((alpha * sx + beta * u) & 1) != 0;
         for (int i = 0; i < n; ++i, ++k) {
-          const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
+          const size_t idx = off + entry_pos(layout, (size_t)bws[w * ns + s], k, lane);
           const int2 e = ent[b0 + i];
           ent_a[idx] = (uint16_t)e.x;
           ent_w[idx] = neg ? -__int_as_float(e.y) : __int_as_float(e.y);
         }
       }
       for (; k < K; ++k) {
-        const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
+        const size_t idx = off + entry_pos(layout, (size_t)bws[w * ns + s], k, lane);
         ent_a[idx] = 0;
         ent_w[idx] = 0.f;
       }
       continue;
     }
     for (int k = 0; k < K; ++k) {
-      const size_t idx = off + (size_t)bws[w * ns + s] + 32 * k + lane;
+      const size_t idx = off + entry_pos(layout, (size_t)bws[w * ns + s], k, lane);
       if (k < cnt[s]) {
         const int2 e = ent[beg[s] + k];
         ent_a[idx] = (uint16_t)e.x;

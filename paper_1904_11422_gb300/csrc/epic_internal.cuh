@@ -54,6 +54,18 @@ enum : int { kLayoutFft64 = 0, kLayoutFft32 = 1, kLayoutPair64 = 3, kLayoutFft12
 // Layouts whose table set 4 c + q gathers the 128 x 128 grid of channel c folded
 // into the 64 x 64 field H_q of output-parity subset q.
 __host__ __device__ inline bool layout_folded(int layout) { return layout == kLayoutPairQ || layout == kLayoutFft64Q; }
+// Position of entry k of lane `lane` in the (warp, slot) range starting at
+// `base`.  The FFT kernels' layouts (kFft64, kFft32, kFft64Q) walk entries two at
+// a time and store each lane's entries 2j and 2j + 1 side by side, so that one
+// 32-bit load fetches both antennas and one 8-byte load both weights:
+// base + 64 (k / 2) + 2 lane + k % 2 (base and every trip count are even).  The
+// other layouts keep entry k of every lane together: base + 32 k + lane.
+__host__ __device__ inline bool layout_paired(int layout) {
+  return layout == kLayoutFft64 || layout == kLayoutFft32 || layout == kLayoutFft64Q;
+}
+__host__ __device__ inline size_t entry_pos(int layout, size_t base, int k, int lane) {
+  return layout_paired(layout) ? base + 64 * (size_t)(k >> 1) + 2 * lane + (k & 1) : base + 32 * (size_t)k + lane;
+}
 struct GatherTables {
   int layout = 0, threads = 0;
   int max_chan_entries = 0;      // padded entries of the largest channel
