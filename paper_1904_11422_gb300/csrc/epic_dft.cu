@@ -539,6 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int K = cnt_s[warp * 8 + s];
         const int b = base_s[warp * 8 + s] + lane;
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
+#pragma unroll 2
         for (int k = 0; k < K; ++k) {
           const float w = EW[b + 32 * k];
           const float4 ev = E4[EA[b + 32 * k]];
@@ -635,15 +636,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t accum2 = 0;
     const uint32_t d1 = tmem + lane_base + kColD1 + 32 * cq;
     const int zrow = cg * kN + ck;
-    auto convert_z = [&](int half) {
-      float v[16];
-      if (__all_sync(0xffffffffu, ok1)) {
-        tmem_ld16(d1 + 16 * half, v);
-        tmem_wait_ld();
-      } else {
+    // both halves of the thread's stage-1 row read at once (one wait)
+    float vz[2][16];
+    if (__all_sync(0xffffffffu, ok1)) {
+      tmem_ld16(d1, vz[0]);
+      tmem_ld16(d1 + 16, vz[1]);
+      tmem_wait_ld();
+    } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = 0.f;
-      }
+      for (int k = 0; k < 16; ++k) vz[0][k] = vz[1][k] = 0.f;
+    }
+    auto convert_z = [&](int half) {
+      float (&v)[16] = vz[half];
       if constexpr (!kBf) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] *= sc_z;
