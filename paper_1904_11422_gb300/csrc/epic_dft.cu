@@ -23,10 +23,9 @@
 // the gather tables and the reduction; the kernel is the same).
 //
 // The samples of a CTA are software-pipelined: the stage-2 products of sample t
-// run while sample t+1 is unpacked and gridded (the first half of them already
-// while the second half of Z is converted), the stage-1 products of t+1 run while
-// sample t is squared and accumulated, and sample t+2's fields are unpacked while
-// stage 1 of t+1 runs.
+// run while sample t+1 is gridded, the stage-1 products of t+1 run while sample t
+// is squared and accumulated, and sample t+2's fields are unpacked while stage 1
+// of t+1 runs.
 //
 // One elected thread issues the MMAs and commits them to mbarriers; every wait
 // on them is bounded (about one second) and reports EPIC_ERR_TIMEOUT through the
@@ -628,10 +627,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // 5. Z = D1 -> stage-2 B operand rows (g, k), K = (c, y), split hi/lo (the
     //    previous sample's stage-2 products, which read this buffer, are
     //    complete), and 6. stage 2: D2[buf] = Fre . Z^T, lanes (j, c), columns
-    //    (g, k), which runs while the next sample is unpacked and gridded.  Both
-    //    in two halves along K: a thread's first 16 y values are the K steps
-    //    0, 2, 4, 6, its last 16 the steps 1, 3, 5, 7, so the products of the
-    //    first half run while the second half is converted.
+    //    (g, k), which runs while the next sample is unpacked and gridded.  The
+    //    conversion is done in two halves along K (a thread's first 16 y values
+    //    are the K steps 0, 2, 4, 6, its last 16 the steps 1, 3, 5, 7).
     const bool ok1 = wait_or_abort(bar1, ph1);
     uint32_t accum2 = 0;
     const uint32_t d1 = tmem + lane_base + kColD1 + 32 * cq;
@@ -646,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int k = 0; k < 16; ++k) vz[0][k] = vz[1][k] = 0.f;
     }
-    auto convert_z = [&](int half) {
+    auto convert_z = [&](int half, bool sync) {
       float (&v)[16] = vz[half];
       if constexpr (!kBf) {
 #pragma unroll
@@ -669,9 +667,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           *reinterpret_cast<uint4*>(sm + DftSmem::B2 + (2 + cc) * kSlab + off) =
               make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
+      if (sync) {
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+      }
     };
     auto issue_stage2 = [&](int half) {
       if (tid == 0) {
@@ -693,10 +693,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (half == 1) ++n_commit2;
     };
-    convert_z(0);
+    // both halves converted before one CTA barrier (a barrier between them, to start
+    // the first half's products early, measured slower), then all of stage 2
+    convert_z(0, false);
+    convert_z(1, true);
     if (*abort_flag) break;  // no wait lies between here and the commit below
     issue_stage2(0);
-    convert_z(1);
     issue_stage2(1);
     have_prev = 1;
     prev_buf = d2buf;

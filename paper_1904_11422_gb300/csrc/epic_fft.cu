@@ -792,6 +792,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
         const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (base_s[warp * 8 + n2] >> 1) + lane;
         const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (base_s[warp * 8 + n2] >> 1) + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
+#pragma unroll 2
         for (int k = 0; k < K; k += 2) {  // the imaging kernel's entry pairs, in the same order
           const uint32_t aa = ea2[16 * k];
           const float2 ww = ew2[16 * k];

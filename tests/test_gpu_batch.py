@@ -9,6 +9,12 @@ from _helpers import TOL, assert_close, oracle_image, rel_errors
 
 pytestmark = pytest.mark.gpu
 
+# A tuned batch splits each call into other time tiles than a single call, so
+# its partial images are summed in another order: the images agree to FP32
+# rounding of the raw (unsubtracted) sums, a few ulps of a raw peak that can be
+# several times the subtracted peak these errors are relative to.
+REORDER_TOL = 5e-6
+
 
 @pytest.fixture(scope="module", autouse=True)
 def lib():
@@ -70,7 +76,7 @@ def test_autotuned_batch_matches_oracle(arrays):
     epic.epic_batch_launch(b)
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
-        assert rel_errors(o.cpu().numpy(), r, 2).max() <= 1e-6
+        assert rel_errors(o.cpu().numpy(), r, 2).max() <= REORDER_TOL
     # arrays A and C against the oracle on two channels each
     for k, chans in ((0, [0, 15]), (3, [0, 31])):
         got = outs[k].cpu().numpy()
@@ -101,7 +107,7 @@ def test_tensor_batch_matches_single_calls(arrays):
     epic.epic_batch_launch(b)
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
-        assert rel_errors(o.cpu().numpy(), r, 2).max() <= 1e-6
+        assert rel_errors(o.cpu().numpy(), r, 2).max() <= REORDER_TOL
     for k, chans in ((0, [0, 15]), (2, [0, 31])):
         got = outs[k].cpu().numpy()
         assert rel_errors(got[chans], oracle_image(ws[k], channels=chans, use_fft=True), 2).max() <= TOL["dft_bf16x3"]
