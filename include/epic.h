@@ -297,6 +297,19 @@ epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_
 /* One launch of the batch's graph on stream (asynchronous). */
 epic_status epic_batch_launch(epic_batch* batch, void* stream);
 
+/* Debug: the failure path of a batch's bounded-spin reduction claims.  (No
+ * counterpart in the paper: the test hook of the library's own failure
+ * detection.)  Runs, outside the batch's graph, the persistent launch of every
+ * tensor-core family whose reductions run in the launch, with each reduction
+ * item waiting for one completion signal more than its imaging items send,
+ * limited to wait_ns (1 000 .. 1 000 000 000).  The imaging items complete; every
+ * reduction item gives up, sets its plan's device status to a time-out and skips
+ * its rows (the outputs are left unspecified).  The next epic_sync of a member
+ * plan returns EPIC_ERR_TIMEOUT and clears the status; the batch and its plans
+ * are usable as before.  EPIC_ERR_UNSUPPORTED when no family of the batch reduces
+ * in its launch. */
+epic_status epic_debug_batch_timeout(epic_batch* batch, long long wait_ns, void* stream);
+
 /* Frees the batch (synchronises the device); the plans are not destroyed. */
 epic_status epic_batch_destroy(epic_batch* batch);
 

@@ -143,14 +143,18 @@ cudaError_t prepare_family(epic_batch* b, TensorFamily& f, int mult, bool inkern
 // The launches of one family: reset the claim and completion counters, then
 // one persistent launch that images every member's time tiles and reduces every
 // member's channels (a member with no samples gets its output zeroed).
-cudaError_t family_launches(epic_batch* b, const TensorFamily& f, cudaStream_t s) {
+// test_wait_ns > 0 (failure test): every reduction item waits for one signal
+// more than can come, for at most test_wait_ns.
+cudaError_t family_launches(epic_batch* b, const TensorFamily& f, cudaStream_t s,
+                            unsigned long long test_wait_ns = 0) {
   const float2* twiddle = nullptr;
   for (int i : f.members)
     if (b->plans[i]->p.N == 128) twiddle = b->plans[i]->p.d_twiddle;
   cudaError_t e = cudaMemsetAsync(f.d_head, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.d_done, 0, sizeof(int) * f.n_done, s);
   if (e == cudaSuccess && f.n_items > 0) {
-    const epic::DftQueue q{f.d_jobs, (int)f.members.size(), f.n_items, f.n_image_items, f.d_head};
+    const epic::DftQueue q{f.d_jobs, (int)f.members.size(), f.n_items, f.n_image_items, f.d_head,
+                           test_wait_ns ? 1 : 0, test_wait_ns};
     e = epic::launch_dft_batch(f.xform, q, f.A_lay, f.max_ent, b->plans[f.members[0]]->p.d_fmat, twiddle,
                                std::min(f.ctas, f.n_items), s);
   }
@@ -435,6 +439,20 @@ epic_status epic_batch_create(epic_plan* const* plans, int n_plans, const uint8_
   if (chosen_ctas)
     for (int i = 0; i < n_plans; ++i) chosen_ctas[i] = b->ctas[i];
   *out = b;
+  return EPIC_OK;
+}
+
+epic_status epic_debug_batch_timeout(epic_batch* b, long long wait_ns, void* stream) {
+  if (!b || wait_ns < 1000 || wait_ns > 1000000000LL) return EPIC_ERR_INVALID_ARG;
+  bool any = false;
+  for (const TensorFamily& f : b->families) any = any || (f.inkernel && f.n_items > f.n_image_items);
+  if (!any) return EPIC_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (const TensorFamily& f : b->families) {
+    if (!(f.inkernel && f.n_items > f.n_image_items)) continue;
+    const cudaError_t e = family_launches(b, f, s, (unsigned long long)wait_ns);
+    if (e != cudaSuccess) return status_of(e);
+  }
   return EPIC_OK;
 }
 

@@ -230,6 +230,10 @@ struct DftQueue {
   int n_jobs, n_items;  // all items: imaging items first, then reduction items
   int n_image_items;
   int* head;  // the next unclaimed item; zero when the launch starts
+  // failure test only: reduction items wait for this many signals more than can
+  // come, for at most wait_ns (0: the normal one-second limit, no extra)
+  int test_extra = 0;
+  unsigned long long wait_ns = 0;
 };
 
 // Pixels of one row per thread in the reduction items of a batch launch.

@@ -86,6 +86,7 @@ SIGNATURES = {
                                _I, ctypes.POINTER(_I), _P, ctypes.POINTER(_P)]),
     "epic_batch_launch": (_I, [_P, _P]),
     "epic_batch_destroy": (_I, [_P]),
+    "epic_debug_batch_timeout": (_I, [_P, ctypes.c_longlong, _P]),
     "epic_status_string": (ctypes.c_char_p, [_I]),
     "epic_debug_unpack": (_I, [_P, ctypes.c_size_t, _P, _P]),
     "epic_debug_grid": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
@@ -384,6 +385,13 @@ def epic_batch_create(plans, d_volts, n_time, d_out, tune: bool = False, stream=
 
 def epic_batch_launch(batch: Batch, stream=None) -> None:
     _check(load_library().epic_batch_launch(batch.handle, _stream(stream)), "epic_batch_launch")
+
+
+def epic_debug_batch_timeout(batch: Batch, wait_ns: int, stream=None) -> None:
+    """The batch's tensor-core families with reduction waits that cannot succeed
+    (see include/epic.h); the members' next epic_sync raises EPIC_ERR_TIMEOUT."""
+    _check(load_library().epic_debug_batch_timeout(batch.handle, int(wait_ns), _stream(stream)),
+           "epic_debug_batch_timeout")
 
 
 def epic_batch_destroy(batch) -> None:

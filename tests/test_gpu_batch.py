@@ -149,3 +149,44 @@ def test_tensor_families_in_one_persistent_launch_bit_for_bit(arrays):
     b.close()
     for p in plans:
         p.close()
+
+
+def test_batch_reduction_wait_times_out_and_the_batch_recovers(arrays):
+    """A family's reduction items wait (bounded spin) for their channels' imaging
+    items to signal; with one signal more expected than can come and a 2 ms
+    limit, every reduction item must give up, its plan's epic_sync report
+    EPIC_ERR_TIMEOUT, and the next launch of the same batch image as before."""
+    import time
+
+    import torch
+    ws = [arrays[0], arrays[2]]
+    plans, vols, outs = _setup(ws, ["dft_bf16x3", "dft_bf16x3"])
+    ref = _single(plans, vols, ws)
+    b = epic.epic_batch_create(plans, vols, [w.n_time for w in ws], outs, tune=False)
+    t0 = time.time()
+    epic.epic_debug_batch_timeout(b, 2_000_000)
+    torch.cuda.synchronize()
+    for p in plans:
+        with pytest.raises(epic.EpicError) as ei:
+            epic.epic_sync(p)
+        assert ei.value.status == epic.EPIC_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    for o in outs:
+        o.fill_(float("nan"))
+    epic.epic_batch_launch(b)
+    torch.cuda.synchronize()
+    for p in plans:
+        epic.epic_sync(p)
+    for o, r in zip(outs, ref):
+        assert np.array_equal(o.cpu().numpy(), r)
+    b.close()
+    for p in plans:
+        p.close()
+    # a batch without tensor-core families has nothing to time out
+    plans, vols, outs = _setup(ws[:1], ["fft_fp32"])
+    b = epic.epic_batch_create(plans, vols, [ws[0].n_time], outs, tune=False)
+    with pytest.raises(epic.EpicError) as ei:
+        epic.epic_debug_batch_timeout(b, 2_000_000)
+    assert ei.value.status == epic.EPIC_ERR_UNSUPPORTED
+    b.close()
+    plans[0].close()
