@@ -427,8 +427,9 @@ def time_grid128(args, epic, synth, torch, stream, world, shard, sms, pk, pk_kin
 
 def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
     """Arrays A, B and C of the batching recipe (T = 1250 each) in one autotuned
-    graph launch, twice: every array on the FP32 path, and every array on the
-    compensated BF16 tensor-core path.  The same plans imaged by separate
+    graph launch, three times: every array on the FP32 path, on the compensated
+    BF16 tensor-core path, and on the plain FP16 tensor-core path (error 1.6e-4 of
+    the image peak on the station block).  The same plans imaged by separate
     epic_image calls one after another are timed for comparison."""
     ws = [synth.batching_array(k) for k in ("A", "B", "C")]
     vols = [torch.from_numpy(w.volts).cuda() for w in ws]
@@ -447,7 +448,8 @@ def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
         return shard.max_over_ranks(e0.elapsed_time(e1) / n, device="cuda")
 
     res = {}
-    for name, xforms in (("fp32", ["fft_fp32"] * 3), ("tensor", ["dft_bf16x3"] * 3)):
+    for name, xforms in (("fp32", ["fft_fp32"] * 3), ("tensor", ["dft_bf16x3"] * 3),
+                         ("tensor_fp16", ["dft_fp16"] * 3)):
         plans = [epic.plan_for(w, epic.XFORMS[x]) for w, x in zip(ws, xforms)]
         outs = [torch.empty(p.out_shape, dtype=torch.float32, device="cuda") for p in plans]
         b = epic.epic_batch_create(plans, vols, [w.n_time for w in ws], outs, tune=True, stream=stream)
@@ -467,7 +469,7 @@ def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
              # chose, reduces them too, or leaves that to one reduction per plan)
              "imaging_kernels_per_step": sum(x == "fft_fp32" for x in xforms)
                                          + len({x for x in xforms if x != "fft_fp32"})}
-        if name == "tensor":
+        if name != "fp32":
             # issued tensor-core flops of the batch over the graph time (a 32^2
             # image set is one 64^2 transform, a 128^2 one four)
             fl = sum(w.n_chan * w.n_time * (4 if w.grid_n == 128 else 1) * tensor_flops_per_tc(x)
@@ -475,8 +477,9 @@ def time_batch(args, epic, synth, torch, stream, world, shard, pk, pk_kind):
             peak = pk.get("bf16_tflops", 1900.0)
             r["roofline"] = {"bound": "tensor", "achieved": fl / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                              "frac": fl / (ms / 1e3) / 1e12 / peak, "flops_per_launch": fl,
-                             "basis": f"issued BF16 x3 flops of arrays A, B and C over the whole graph time; "
-                                      f"peak: measured dense BF16 cuBLAS burst ({pk_kind})"}
+                             "basis": f"issued {xforms[0]} tensor flops of arrays A, B and C over the whole "
+                                      f"graph time; peak: measured dense BF16 cuBLAS burst ({pk_kind}; "
+                                      f"FP16 dense rate taken equal)"}
         else:
             # algorithmic FP32 flops of the batch (each grid's transform counted as
             # one N x N FFT, as in the single-plan rooflines) over the graph time

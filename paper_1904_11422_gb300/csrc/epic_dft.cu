@@ -374,8 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the two bytes of each of the thread's antennas (a = tid + 512 k < A <= 1024),
   // prefetched one sample ahead so that the unpack never waits for HBM; packed
   // as antenna tid in the low and antenna tid + 512 in the high half
-  auto load_raw = [&](long long u) -> unsigned {
-    const int c = (int)(u / jp->T), t = (int)(u % jp->T);
+  auto load_raw = [&](int c, int t) -> unsigned {
     const int cr = q128 ? c >> 2 : c;
     const unsigned short* base =
         reinterpret_cast<const unsigned short*>(jp->volts + ((size_t)t * jp->C + cr) * (size_t)jp->A * 2);
@@ -458,11 +457,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     u1 = min(u0 + jp->W, jp->units);
     if (u0 >= u1) continue;
     c_first = (int)(u0 / jp->T);
-    raw = load_raw(u0);
+    // unit u = (channel cu, sample tu), stepped without 64-bit divisions
+    int cu = c_first, tu = (int)(u0 - (long long)c_first * jp->T);
+    raw = load_raw(cu, tu);
     have_next = false;
     cur_c = -1;
   for (long long u = u0; u < u1; ++u) {
-    const int c = (int)(u / jp->T);
+    const int c = cu;
+    int cn = cu, tn = tu + 1;  // the next unit
+    if (tn == jp->T) {
+      tn = 0;
+      ++cn;
+    }
     if (c != cur_c) {
       if (have_prev) {  // the last sample of the previous channel still owes its squares
         const bool ok2 = wait_or_abort(bar2, ph2);
@@ -517,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
     }
 
-    if (u + 1 < u1) raw_next = load_raw(u + 1);
+    if (u + 1 < u1) raw_next = load_raw(cn, tn);
 
     if (!have_next) {
       unpack(raw);
@@ -628,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool ok2 = wait_or_abort(bar2, ph2);
       epilogue(prev_buf, ok2);
     }
-    if (u + 1 < u1 && (int)((u + 1) / jp->T) == c) {
+    if (u + 1 < u1 && cn == c) {
       unpack(raw_next);
       have_next = true;
     }
@@ -713,6 +719,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     prev_buf = d2buf;
     d2buf ^= 1;
     raw = raw_next;
+    cu = cn;
+    tu = tn;
   }
   // ---- end of the item: the last sample's squares, then its channel's partial
   if (*abort_flag) break;  // read after the loop's last CTA barrier: every thread agrees

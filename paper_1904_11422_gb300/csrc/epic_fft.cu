@@ -201,10 +201,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
 #pragma unroll
     for (int s = 0; s < 8; ++s) acc[pl][s] = 0.f;
 
-  // raw bytes of the thread's antennas, prefetched one unit ahead
+  // raw bytes of the thread's antennas, prefetched one unit ahead; unit u is
+  // (channel cu, sample tu), stepped without 64-bit divisions
   unsigned raw[MAXK] = {}, raw_next[MAXK] = {};
-  auto load_raw = [&](long long u, unsigned (&dst)[MAXK]) {
-    const int c = (int)(u / T) >> (Q ? 2 : 0), t = (int)(u % T);
+  int cu = c_first, tu = (int)(u0 - (long long)c_first * T);
+  auto load_raw = [&](int cv, int t, unsigned (&dst)[MAXK]) {
+    const int c = cv >> (Q ? 2 : 0);
     const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
 #pragma unroll
     for (int k = 0; k < MAXK; ++k) {
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
       }
     }
   };
-  load_raw(u0, raw);
+  load_raw(cu, tu, raw);
 
   int cur_c = -1;
   const uint16_t* ent_a = g_ent_a;
@@ -241,7 +243,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
   };
 
   for (long long u = u0; u < u1; ++u) {
-    const int c = (int)(u / T);
+    const int c = cu;
+    int cn = cu, tn = tu + 1;  // the next unit
+    if (tn == T) {
+      tn = 0;
+      ++cn;
+    }
     if (c != cur_c) {
       if (cur_c >= 0) {
         flush(cur_c);
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
       }
       __syncthreads();
     }
-    if (u + 1 < u1) load_raw(u + 1, raw_next);
+    if (u + 1 < u1) load_raw(cn, tn, raw_next);
 
     // 1. unpack, calibrate, exact integer self powers
 #pragma unroll
@@ -377,6 +384,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     }
 #pragma unroll
     for (int k = 0; k < MAXK; ++k) raw[k] = raw_next[k];
+    cu = cn;
+    tu = tn;
   }
   flush(cur_c);
 }
@@ -712,8 +721,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     }
   };
 
+  int cu = c_first, tu = (int)(u0 - (long long)c_first * T);  // unit u = (channel cu, sample tu)
   for (long long u = u0; u < u1; ++u) {
-    const int c = (int)(u / T), t = (int)(u % T);
+    const int c = cu, t = tu;
+    if (++tu == T) {
+      tu = 0;
+      ++cu;
+    }
     const int cr = Q ? c >> 2 : c;  // the plan's channel (c is a virtual channel when folded)
     if (c != cur_c) {
       if (cur_c >= 0) {

@@ -206,9 +206,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr size_t kXSlab = (size_t)P * kRows * kRows;  // float2 per (parity, writer)
   float2* xb = xbuf + (size_t)cluster * 4 * kXSlab;
 
+  // unit u = (channel cu, sample tu), stepped without 64-bit divisions
   unsigned raw[kMaxK] = {}, raw_next[kMaxK] = {};
-  auto load_raw = [&](long long u, unsigned (&dst)[kMaxK]) {
-    const int c = (int)(u / T), t = (int)(u % T);
+  int cu = c_first, tu = (int)(u0 - (long long)c_first * T);
+  auto load_raw = [&](int c, int t, unsigned (&dst)[kMaxK]) {
     const uint8_t* base = volts + ((size_t)t * C + c) * (size_t)A * P;
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k) {
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   };
-  load_raw(u0, raw);
+  load_raw(cu, tu, raw);
 
   auto zero_acc = [&]() {
     uint32_t z[16];
@@ -284,7 +285,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const float* ent_w = g_ent_w;
 
   for (long long u = u0; u < u1; ++u) {
-    const int c = (int)(u / T);
+    const int c = cu;
+    int cn = cu, tn = tu + 1;  // the next unit
+    if (tn == T) {
+      tn = 0;
+      ++cn;
+    }
     if (c != cur_c) {
       if (cur_c >= 0) flush(cur_c);
       zero_acc();
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
     }
-    if (u + 1 < u1) load_raw(u + 1, raw_next);
+    if (u + 1 < u1) load_raw(cn, tn, raw_next);
 
     // E holds this sample's fields already when they were unpacked while the
     // previous sample waited at its cluster barrier
@@ -381,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // sample of the same channel (every thread has finished reading E)
     __syncthreads();
     cluster_arrive();
-    if (u + 1 < u1 && (int)((u + 1) / T) == c) {
+    if (u + 1 < u1 && cn == c) {
       unpack(raw_next);
       have_next = true;
     }
@@ -445,6 +451,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k) raw[k] = raw_next[k];
+    cu = cn;
+    tu = tn;
     // the next unit's unpack and row pass reuse E and the row buffers
     __syncthreads();
   }

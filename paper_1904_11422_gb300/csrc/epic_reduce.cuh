@@ -39,12 +39,24 @@ __device__ __forceinline__ void reduce_rows(const ReduceArgs& r, int cv, int j0,
   const long long W = r.W, T = r.T;
   const long long b_lo = ((long long)cv * T) / W;
   const long long b_hi = min(((long long)(cv + 1) * T - 1) / W, (long long)r.ctas - 1);
+  // CTA b's first channel floor(b W / T) (its partials' slot 0), stepped over b
+  // from b_lo with additions only: b W = q T + rem
+  const long long q_lo = (b_lo * W) / T, rem_lo = b_lo * W - q_lo * T, wq = W / T, wr = W - wq * T;
+  auto next_b = [&](long long& q, long long& rem) {
+    rem += wr;
+    q += wq;
+    if (rem >= T) {
+      rem -= T;
+      ++q;
+    }
+  };
 
   if (r.subtract) {
     for (int a = tid; a < A; a += nthreads) {
       long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      for (long long b = b_lo; b <= b_hi; ++b) {
-        const int slot = cv - (int)((b * W) / T);
+      long long q = q_lo, rem = rem_lo;
+      for (long long b = b_lo; b <= b_hi; ++b, next_b(q, rem)) {
+        const int slot = cv - (int)q;
         const int4 v = __ldcg(reinterpret_cast<const int4*>(r.part_auto) + (b * r.spans + slot) * A + a);
         s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
       }
@@ -73,8 +85,9 @@ __device__ __forceinline__ void reduce_rows(const ReduceArgs& r, int cv, int j0,
     for (int e = 0; e < kReducePix; ++e) {
       const int pix = dec * (j0 + jj) * Ns + dec * (i0 + e);
       s[e][0] = s[e][1] = s[e][2] = s[e][3] = 0.f;
-      for (long long b = b_lo; b <= b_hi; ++b) {
-        const int slot = cv - (int)((b * W) / T);
+      long long q = q_lo, rem = rem_lo;
+      for (long long b = b_lo; b <= b_hi; ++b, next_b(q, rem)) {
+        const int slot = cv - (int)q;
         const float* src = r.part + (size_t)(b * r.spans + slot) * 4 * NNs + pix;
         s[e][0] += __ldcg(src);
         if (P == 2) {
