@@ -70,11 +70,16 @@ __device__ __forceinline__ int field_count(int layout, const int* ptr, int N, in
 
 // kLayoutPair64 / kLayoutPairQ: the 2048 cell pairs (y, 2r..2r+1) of a 64 x 64
 // field, ranked by their number of entries (descending, ties by index) and dealt
-// to the 512 threads in snake order, four per thread: thread t gets the pairs of
-// rank j*512 + t (j even) or j*512 + 511 - t (j odd), j = 0..3, so every thread's
-// total is close to the mean.  Slot s of the thread is cell (s & 1) of its pair
-// s >> 1.  pair_of[t*4 + j] receives pair index y*32 + r.
-__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int* loads, int* perm, int* pair_of) {
+// four per thread in snake order, so that every thread's total is close to the
+// mean: thread t0 + t gets the pairs of rank j*n + t (j even) or j*n + n - 1 - t
+// (j odd), j = 0..3, over n = 512 - t0 threads.  With spare0 (the hi + lo
+// transforms, whose 48 MMA instructions per sample hold warp 0's issuing lane
+// about as long as they run), warp 0 instead takes the 128 lightest pairs (ranks
+// 1920..2047, most of them empty cells outside the aperture) and the snake
+// starts at t0 = 32.  Slot s of a thread is cell (s & 1) of its pair s >> 1.
+// pair_of[t*4 + j] receives pair index y*32 + r.
+__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare0, int* loads, int* perm,
+                           int* pair_of) {
   for (int q = tid; q < 2048; q += 512) {
     const int y = q >> 5, r = q & 31;
     loads[q] = field_count(layout, ptr, N, y, 2 * r) + field_count(layout, ptr, N, y, 2 * r + 1);
@@ -87,13 +92,21 @@ __device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int* load
     perm[rank] = q;
   }
   __syncthreads();
-  for (int j = 0; j < 4; ++j) pair_of[tid * 4 + j] = perm[j * 512 + ((j & 1) ? 511 - tid : tid)];
+  const int t0 = spare0 ? 32 : 0, n = 512 - t0;
+  for (int j = 0; j < 4; ++j) {
+    if (tid >= t0) {
+      const int t = tid - t0;
+      pair_of[tid * 4 + j] = perm[j * n + ((j & 1) ? n - 1 - t : t)];
+    } else {
+      pair_of[tid * 4 + j] = perm[4 * n + j * 32 + ((j & 1) ? 31 - tid : tid)];
+    }
+  }
   __syncthreads();
 }
 
 // One CTA of nt threads per channel.  fill = 0: only the padded entry count of
 // the channel (tot[c]); fill = 1: also every table.
-__global__ void gather_tables_kernel(int layout, int N, int nnz, int fill, const int* __restrict__ csr_ptr,
+__global__ void gather_tables_kernel(int layout, int spare0, int N, int nnz, int fill, const int* __restrict__ csr_ptr,
                                      const int2* __restrict__ csr_ent, const int* __restrict__ chan_off,
                                      int* __restrict__ tot, int* __restrict__ cnt_out, int* __restrict__ base_out,
                                      uint16_t* __restrict__ task_out, uint16_t* __restrict__ ent_a,
@@ -116,7 +129,7 @@ __global__ void gather_tables_kernel(int layout, int N, int nnz, int fill, const
   int task = tid;
   int2 cells[16];
   if (pairs) {
-    deal_pairs(layout, ptr, N, tid, keys, perm, pair_of);
+    deal_pairs(layout, ptr, N, tid, spare0, keys, perm, pair_of);
     for (int s = 0; s < 8; ++s) {
       const int q = pair_of[tid * 4 + (s >> 1)];
       cells[s] = make_int2(q >> 5, 2 * (q & 31) + (s & 1));
@@ -209,12 +222,14 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* total_
   const int nnz = p.A * p.S * p.S;
   const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
   const int nsets = layout_folded(layout) ? 4 * p.C : p.C;  // table sets (virtual channels)
+  // the tensor-core hi + lo transforms spare warp 0 (the products' issuer) the gathering
+  const int spare0 = pairs && (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_FP16X3);
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
                                      (pairs ? 2 * 2048 + 4 * (size_t)threads : 0));
   int* d_tot = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * nsets);
   if (e != cudaSuccess) return e;
-  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, spare0, p.N, nnz, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
                                                nullptr, nullptr, nullptr, nullptr, nullptr);
   e = cudaGetLastError();
   std::vector<int> tot(nsets);
@@ -245,7 +260,7 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* total_
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_w), sizeof(float) * total)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (nsets + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
-  gather_tables_kernel<<<nsets, threads, smem>>>(layout, p.N, nnz, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, spare0, p.N, nnz, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
                                                nullptr, g.d_cnt, g.d_base, g.d_task, g.d_ent_a, g.d_ent_w);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
