@@ -68,39 +68,95 @@ __device__ __forceinline__ int field_count(int layout, const int* ptr, int N, in
   return n;
 }
 
-// kLayoutPair64 / kLayoutPairQ: the 2048 cell pairs (y, 2r..2r+1) of a 64 x 64
-// field, ranked by their number of entries (descending, ties by index) and dealt
-// four per thread in snake order, so that every thread's total is close to the
-// mean: thread t0 + t gets the pairs of rank j*n + t (j even) or j*n + n - 1 - t
-// (j odd), j = 0..3, over n = 512 - t0 threads.  With spare0 (the hi + lo
-// transforms, whose 48 MMA instructions per sample hold warp 0's issuing lane
-// about as long as they run), warp 0 instead takes the 128 lightest pairs (ranks
-// 1920..2047, most of them empty cells outside the aperture) and the snake
-// starts at t0 = 32.  Slot s of a thread is cell (s & 1) of its pair s >> 1.
-// pair_of[t*4 + j] receives pair index y*32 + r.
-__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare0, int* loads, int* perm,
-                           int* pair_of) {
+// kLayoutPair64 / kLayoutPairQ / kLayoutPairD: the 2048 cell pairs
+// (y, 2r..2r+1) of a 64 x 64 field, dealt four per thread.  Slot s of a thread
+// is cell (s & 1) of its pair s >> 1, and a warp's gather costs, per slot, the
+// largest entry count over its 32 lanes, so a warp costs
+//   sum over its four pair slots j of (max K(cell 0) + max K(cell 1)),
+// and the block's slowest warp sets the time.  The pairs are ranked by
+// (K(cell 0), K(cell 1)) (descending, ties by index) and cut into blocks of 32
+// consecutive ranks, whose lanes then hold near-equal counts; the blocks are
+// dealt to the warps largest cost first, each to the cheapest warp with a free
+// pair slot, and then blocks of the costliest warp are swapped with cheaper
+// blocks of other warps while that lowers the largest warp cost.  With spare0
+// (the hi + lo transforms, whose 48 MMA instructions per sample hold warp 0's
+// issuing lane about as long as they run) warp 0 takes no block: it gets the
+// 128 lowest-ranked pairs (mostly empty cells outside the aperture).
+// pair_of[t*4 + j] receives pair index y*32 + r.  smem: keys [2048], perm
+// [2048], bcost [64], bslot [64].
+__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare0, int* keys, int* perm,
+                           int* bcost, int* bslot, int* pair_of) {
   for (int q = tid; q < 2048; q += 512) {
     const int y = q >> 5, r = q & 31;
-    loads[q] = field_count(layout, ptr, N, y, 2 * r) + field_count(layout, ptr, N, y, 2 * r + 1);
+    keys[q] = field_count(layout, ptr, N, y, 2 * r) * 8192 + field_count(layout, ptr, N, y, 2 * r + 1);
   }
   __syncthreads();
   for (int q = tid; q < 2048; q += 512) {
-    const int L = loads[q];
+    const int L = keys[q];
     int rank = 0;
-    for (int j = 0; j < 2048; ++j) rank += (loads[j] > L) || (loads[j] == L && j < q);
+    for (int j = 0; j < 2048; ++j) rank += (keys[j] > L) || (keys[j] == L && j < q);
     perm[rank] = q;
   }
   __syncthreads();
-  const int t0 = spare0 ? 32 : 0, n = 512 - t0;
-  for (int j = 0; j < 4; ++j) {
-    if (tid >= t0) {
-      const int t = tid - t0;
-      pair_of[tid * 4 + j] = perm[j * n + ((j & 1) ? n - 1 - t : t)];
-    } else {
-      pair_of[tid * 4 + j] = perm[4 * n + j * 32 + ((j & 1) ? 31 - tid : tid)];
+  const int w0 = spare0 ? 1 : 0, nw = 16 - w0, nb = 4 * nw;  // dealing warps, blocks
+  if (tid < nb) {
+    int m0 = 0, m1 = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int k = keys[perm[32 * tid + l]];
+      m0 = max(m0, k / 8192);
+      m1 = max(m1, k % 8192);
+    }
+    bcost[tid] = m0 + m1;
+    bslot[tid] = -1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int wcost[16], wfill[16];
+    for (int w = 0; w < 16; ++w) wcost[w] = wfill[w] = 0;
+    for (int it = 0; it < nb; ++it) {  // largest block first, to the cheapest warp with room
+      int b = -1;
+      for (int k = 0; k < nb; ++k)
+        if (bslot[k] < 0 && (b < 0 || bcost[k] > bcost[b])) b = k;
+      int w = -1;
+      for (int x = 0; x < nw; ++x)
+        if (wfill[x] < 4 && (w < 0 || wcost[x] < wcost[w])) w = x;
+      bslot[b] = 4 * w + wfill[w]++;
+      wcost[w] += bcost[b];
+    }
+    for (int round = 0; round < 256; ++round) {  // swaps that lower the costliest warp
+      int wm = 0;
+      for (int x = 1; x < nw; ++x)
+        if (wcost[x] > wcost[wm]) wm = x;
+      int best = wcost[wm], bi = -1, bk = -1;
+      for (int i = 0; i < nb; ++i) {
+        if (bslot[i] / 4 != wm) continue;
+        for (int k = 0; k < nb; ++k) {
+          const int w = bslot[k] / 4;
+          if (w == wm || bcost[k] >= bcost[i]) continue;
+          const int nm = max(wcost[wm] - bcost[i] + bcost[k], wcost[w] - bcost[k] + bcost[i]);
+          if (nm < best) {
+            best = nm;
+            bi = i;
+            bk = k;
+          }
+        }
+      }
+      if (bi < 0) break;
+      const int wk = bslot[bk] / 4, d = bcost[bi] - bcost[bk];
+      wcost[wm] -= d;
+      wcost[wk] += d;
+      const int t = bslot[bi];
+      bslot[bi] = bslot[bk];
+      bslot[bk] = t;
     }
   }
+  __syncthreads();
+  for (int b = 0; b < nb; ++b) {  // block b to lanes of warp w0 + bslot / 4, pair slot bslot % 4
+    const int w = w0 + bslot[b] / 4, j = bslot[b] % 4;
+    if (tid >> 5 == w) pair_of[tid * 4 + j] = perm[32 * b + (tid & 31)];
+  }
+  if (tid < 32 * w0)
+    for (int j = 0; j < 4; ++j) pair_of[tid * 4 + j] = perm[32 * nb + 32 * j + tid];
   __syncthreads();
 }
 
@@ -120,6 +176,8 @@ __global__ void gather_tables_kernel(int layout, int spare0, int N, int nnz, int
   int* keys = bws + warps * ns;  // [2048] (pairs only)
   int* perm = keys + 2048;       // [2048] (pairs only)
   int* pair_of = perm + 2048;    // [4 nt] (pairs only)
+  int* bcost = pair_of + 4 * nt; // [64] (pairs only)
+  int* bslot = bcost + 64;       // [64] (pairs only)
   // table set (channel, or virtual channel 4 c + q) and the grid channel it reads
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int cg = layout_folded(layout) ? c >> 2 : c;
@@ -129,7 +187,7 @@ __global__ void gather_tables_kernel(int layout, int spare0, int N, int nnz, int
   int task = tid;
   int2 cells[16];
   if (pairs) {
-    deal_pairs(layout, ptr, N, tid, spare0, keys, perm, pair_of);
+    deal_pairs(layout, ptr, N, tid, spare0, keys, perm, bcost, bslot, pair_of);
     for (int s = 0; s < 8; ++s) {
       const int q = pair_of[tid * 4 + (s >> 1)];
       cells[s] = make_int2(q >> 5, 2 * (q & 31) + (s & 1));
@@ -225,7 +283,7 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* total_
   // the tensor-core hi + lo transforms spare warp 0 (the products' issuer) the gathering
   const int spare0 = pairs && (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_FP16X3);
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
-                                     (pairs ? 2 * 2048 + 4 * (size_t)threads : 0));
+                                     (pairs ? 2 * 2048 + 4 * (size_t)threads + 128 : 0));
   int* d_tot = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * nsets);
   if (e != cudaSuccess) return e;
