@@ -78,13 +78,13 @@ __device__ __forceinline__ int field_count(int layout, const int* ptr, int N, in
 // consecutive ranks, whose lanes then hold near-equal counts; the blocks are
 // dealt to the warps largest cost first, each to the cheapest warp with a free
 // pair slot, and then blocks of the costliest warp are swapped with cheaper
-// blocks of other warps while that lowers the largest warp cost.  With spare0
-// (the hi + lo transforms, whose 48 MMA instructions per sample hold warp 0's
-// issuing lane about as long as they run) warp 0 takes no block: it gets the
-// 128 lowest-ranked pairs (mostly empty cells outside the aperture).
-// pair_of[t*4 + j] receives pair index y*32 + r.  smem: keys [2048], perm
-// [2048], bcost [64], bslot [64].
-__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare0, int* keys, int* perm,
+// blocks of other warps while that lowers the largest warp cost.  Warp 0
+// starts with a cost of head entries: its first lane issues the tensor-core
+// products and is held about as long as they run, which the kernel measured at
+// about the time of 8 (hi + lo transforms, 48 MMA instructions per sample) or 4
+// (plain, 16) gathered entries per lane.  pair_of[t*4 + j] receives pair index
+// y*32 + r.  smem: keys [2048], perm [2048], bcost [64], bslot [64].
+__device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int head, int* keys, int* perm,
                            int* bcost, int* bslot, int* pair_of) {
   for (int q = tid; q < 2048; q += 512) {
     const int y = q >> 5, r = q & 31;
@@ -98,7 +98,7 @@ __device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare
     perm[rank] = q;
   }
   __syncthreads();
-  const int w0 = spare0 ? 1 : 0, nw = 16 - w0, nb = 4 * nw;  // dealing warps, blocks
+  constexpr int nw = 16, nb = 64;  // warps, blocks
   if (tid < nb) {
     int m0 = 0, m1 = 0;
     for (int l = 0; l < 32; ++l) {
@@ -113,6 +113,7 @@ __device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare
   if (tid == 0) {
     int wcost[16], wfill[16];
     for (int w = 0; w < 16; ++w) wcost[w] = wfill[w] = 0;
+    wcost[0] = head;
     for (int it = 0; it < nb; ++it) {  // largest block first, to the cheapest warp with room
       int b = -1;
       for (int k = 0; k < nb; ++k)
@@ -151,18 +152,16 @@ __device__ void deal_pairs(int layout, const int* ptr, int N, int tid, int spare
     }
   }
   __syncthreads();
-  for (int b = 0; b < nb; ++b) {  // block b to lanes of warp w0 + bslot / 4, pair slot bslot % 4
-    const int w = w0 + bslot[b] / 4, j = bslot[b] % 4;
+  for (int b = 0; b < nb; ++b) {  // block b to the lanes of warp bslot / 4, pair slot bslot % 4
+    const int w = bslot[b] / 4, j = bslot[b] % 4;
     if (tid >> 5 == w) pair_of[tid * 4 + j] = perm[32 * b + (tid & 31)];
   }
-  if (tid < 32 * w0)
-    for (int j = 0; j < 4; ++j) pair_of[tid * 4 + j] = perm[32 * nb + 32 * j + tid];
   __syncthreads();
 }
 
 // One CTA of nt threads per channel.  fill = 0: only the padded entry count of
 // the channel (tot[c]); fill = 1: also every table.
-__global__ void gather_tables_kernel(int layout, int spare0, int N, int nnz, int fill, const int* __restrict__ csr_ptr,
+__global__ void gather_tables_kernel(int layout, int head, int N, int nnz, int fill, const int* __restrict__ csr_ptr,
                                      const int2* __restrict__ csr_ent, const int* __restrict__ chan_off,
                                      int* __restrict__ tot, int* __restrict__ cnt_out, int* __restrict__ base_out,
                                      uint16_t* __restrict__ task_out, uint16_t* __restrict__ ent_a,
@@ -187,7 +186,7 @@ __global__ void gather_tables_kernel(int layout, int spare0, int N, int nnz, int
   int task = tid;
   int2 cells[16];
   if (pairs) {
-    deal_pairs(layout, ptr, N, tid, spare0, keys, perm, bcost, bslot, pair_of);
+    deal_pairs(layout, ptr, N, tid, head, keys, perm, bcost, bslot, pair_of);
     for (int s = 0; s < 8; ++s) {
       const int q = pair_of[tid * 4 + (s >> 1)];
       cells[s] = make_int2(q >> 5, 2 * (q & 31) + (s & 1));
@@ -280,14 +279,15 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* total_
   const int nnz = p.A * p.S * p.S;
   const bool pairs = layout == kLayoutPair64 || layout == kLayoutPairQ || layout == kLayoutPairD;
   const int nsets = layout_folded(layout) ? 4 * p.C : p.C;  // table sets (virtual channels)
-  // the tensor-core hi + lo transforms spare warp 0 (the products' issuer) the gathering
-  const int spare0 = pairs && (p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_FP16X3);
+  // warp 0's head start in the tensor path's deal (its lane 0 issues the products)
+  const bool x3 = p.xform == EPIC_XFORM_DFT_BF16X3 || p.xform == EPIC_XFORM_DFT_FP16X3;
+  const int head = pairs ? (x3 ? 8 : 4) : 0;
   const size_t smem = sizeof(int) * (2 * (size_t)warps * ns +
                                      (pairs ? 2 * 2048 + 4 * (size_t)threads + 128 : 0));
   int* d_tot = nullptr;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tot), sizeof(int) * nsets);
   if (e != cudaSuccess) return e;
-  gather_tables_kernel<<<nsets, threads, smem>>>(layout, spare0, p.N, nnz, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, head, p.N, nnz, 0, p.d_csr_ptr, p.d_csr_ent, nullptr, d_tot,
                                                nullptr, nullptr, nullptr, nullptr, nullptr);
   e = cudaGetLastError();
   std::vector<int> tot(nsets);
@@ -318,7 +318,7 @@ cudaError_t build_gather_tables(Plan& p, int layout, int threads, size_t* total_
   if ((e = grab(reinterpret_cast<void**>(&g.d_ent_w), sizeof(float) * total)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(g.d_chan_off, off.data(), sizeof(int) * (nsets + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
-  gather_tables_kernel<<<nsets, threads, smem>>>(layout, spare0, p.N, nnz, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
+  gather_tables_kernel<<<nsets, threads, smem>>>(layout, head, p.N, nnz, 1, p.d_csr_ptr, p.d_csr_ent, g.d_chan_off,
                                                nullptr, g.d_cnt, g.d_base, g.d_task, g.d_ent_a, g.d_ent_w);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
