@@ -1,8 +1,9 @@
 """Edge cases of the 128 x 128 and 32 x 32 paths (FP32 clusters, tensor-core
 parity split and zero-padded transform): single samples, more channels than
 clusters or CTAs, time additivity through accumulate = 1, the host-buffer entry
-point, the no-allocation entry point's limits, and host-side fault injection (a
-staging allocation that cannot succeed)."""
+point, the no-allocation entry point's limits, host-side fault injection (a
+staging allocation that cannot succeed), and arrays with most antennas stacked on
+one position (the most uneven gather tables)."""
 import numpy as np
 import pytest
 
@@ -329,3 +330,33 @@ def test_timeout_hook_rejects_fp32_plans_and_bad_limits():
             epic.epic_debug_image_timeout(plan, dv, w.n_time, bad)
         assert ei.value.status == epic.EPIC_ERR_INVALID_ARG
     plan.close()
+
+
+@pytest.mark.parametrize("grid_n", [64, 128])
+@pytest.mark.parametrize("xf", ["fft_fp32", "dft_bf16x3", "dft_fp16x3", "dft_bf16", "dft_fp16"])
+def test_stacked_antennas(xf, grid_n):
+    """160 of 200 antennas at one position: the 25 cells under the stack hold 160
+    entries each while most cells hold none, the most uneven gather tables an
+    array can give (the tensor path's cell-pair deal, the FP32 path's padded
+    trip counts, the FP16 operand scales of a field 160 kernels deep)."""
+    w = synth.random_small(1901, n_ant=200, n_pol=2, n_chan=2, grid_n=grid_n, support=5, n_time=3)
+    w.ant_xy = np.array(w.ant_xy)
+    w.ant_xy[:160] = w.ant_xy[0]
+    for sub in (True, False):
+        got = gpu_image(w, xform=epic.XFORMS[xf], subtract=sub)
+        err = rel_errors(got, oracle_image(w, subtract=sub), 2)
+        assert err.max() <= TOL[xf], (xf, grid_n, sub, err.max())
+
+
+def test_stacked_antennas_on_clusters():
+    """The same stacking on the 128 x 128 two-CTA cluster kernel (450 antennas x
+    25 = 11 250 entries per channel, above the folding threshold), 400 of them at
+    one position."""
+    w = synth.random_small(1902, n_ant=450, n_pol=2, n_chan=1, grid_n=128, support=5, n_time=3)
+    w.ant_xy = np.array(w.ant_xy)
+    w.ant_xy[:400] = w.ant_xy[0]
+    plan = epic.plan_for(w)
+    assert plan.info["cluster_dim"] == 2
+    got = gpu_image(w, plan=plan)
+    plan.close()
+    assert_close(got, oracle_image(w), 2)
