@@ -361,15 +361,17 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     {
       const int k = line;
       float2 v[P][8];
+      // both polarisations' columns loaded before the first transform (its warp
+      // syncs would otherwise hold the second one's loads back)
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
+      for (int p = 0; p < P; ++p)
 #pragma unroll
         for (int m2 = 0; m2 < 8; ++m2) {
           const int y = n1 + R1 * m2;
           v[p][m2] = Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))];
         }
-        fft_line<N>(v[p], tw, scr, r, n1);
-      }
+#pragma unroll
+      for (int p = 0; p < P; ++p) fft_line<N>(v[p], tw, scr, r, n1);
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const float2 X = v[0][s];
