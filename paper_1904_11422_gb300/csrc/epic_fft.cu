@@ -850,14 +850,19 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     {
       const int k = line;
       const int col = (k + HALF) & (N - 1);
+      // both polarisations' columns loaded before the first transform (its warp
+      // syncs would otherwise hold the second one's loads back)
+      float2 vp[P][8];
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        float2 v[8];
+      for (int p = 0; p < P; ++p)
 #pragma unroll
         for (int m2 = 0; m2 < 8; ++m2) {
           const int y = n1 + R1 * m2;
-          v[m2] = Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))];
+          vp[p][m2] = Rbuf[(size_t)p * NN + y * N + (k ^ G::swz(y))];
         }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        float2 (&v)[8] = vp[p];
         fft_line<N>(v, tw, scr, r, n1);
         // thread (k, q = n1) holds Y[j = n1 + 8 s][k]; pixel row (j + N/2) mod N
 #pragma unroll
@@ -897,13 +902,17 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     {
       const int y = line;
       const int sw = G::swz(y);
+      // element n1 + R1 n2 of the row (at N = 64 the same position as rowpos(n1, n2)),
+      // both polarisations loaded first
+      float2 vp[P][8];
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) vp[p][n2] = Rbuf[(size_t)p * NN + y * N + ((n1 + R1 * n2) ^ sw)];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        float2 v[8];
+        float2 (&v)[8] = vp[p];
         float2* Rrow = Rbuf + (size_t)p * NN + y * N;
-        // element n1 + R1 n2 of the row (at N = 64 the same position as rowpos(n1, n2))
-#pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) v[n2] = Rrow[(n1 + R1 * n2) ^ sw];
         fft_line<N>(v, tw, scr, r, n1);
 #pragma unroll
         for (int s = 0; s < 8; ++s) Rrow[G::rowpos(n1, s, sw)] = make_float2(v[s].x, -v[s].y);
