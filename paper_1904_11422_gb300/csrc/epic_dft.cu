@@ -542,11 +542,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       // (unrolled by two when the tables are in shared memory; from L2 the
       // unrolled loop was slower: 11.66 -> 13.49 ms on 1 024 antennas at 128^2)
       auto gather = [&](const uint16_t* EA, const float* EW, auto in_smem) {
+      // the warp's eight trip counts and first entries, read before the first slot
+      int Ks[8], bs[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        Ks[s] = cnt_s[warp * 8 + s];
+        bs[s] = base_s[warp * 8 + s];
+      }
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         // slot s = cell (s & 1) of pair s >> 1: lane-interleaved entries, warp-uniform trip count
-        const int K = cnt_s[warp * 8 + s];
-        const int b = base_s[warp * 8 + s] + lane;
+        const int K = Ks[s];
+        const int b = bs[s] + lane;
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
         auto entry = [&](int k) {
           const float w = EW[b + 32 * k];

@@ -310,14 +310,25 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     {
       const int y = line;
       float2 v[P][8];
+      // the warp's eight trip counts and first entries, read before the first slot
+      // (measured faster except for the folded 128 x 128 grids, which read them per slot)
+      int Ks[8], bs[8];
+      if constexpr (!Q) {
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+          Ks[n2] = cnt_s[warp * 8 + n2];
+          bs[n2] = base_s[warp * 8 + n2];
+        }
+      }
 #pragma unroll
       for (int n2 = 0; n2 < 8; ++n2) {
         // cell (y, n1 + R1 n2): lane-interleaved entries, warp-uniform trip count
-        const int K = cnt_s[warp * 8 + n2];
+        const int K = Q ? cnt_s[warp * 8 + n2] : Ks[n2];
+        const int bse = Q ? base_s[warp * 8 + n2] : bs[n2];
         // a lane's entries 2j, 2j + 1 side by side (entry_pos): one 32-bit load of
         // both antennas, one 8-byte load of both weights
-        const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (base_s[warp * 8 + n2] >> 1) + lane;
-        const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (base_s[warp * 8 + n2] >> 1) + lane;
+        const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (bse >> 1) + lane;
+        const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (bse >> 1) + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
 #pragma unroll 2
         for (int k = 0; k < K; k += 2) {  // K is even: two entries per step, added in order
@@ -802,11 +813,20 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     {
       const int y = line;
       float2 v[P][8];
+      int Ks[8], bs[8];  // read before the first slot, as in the imaging kernel
+      if constexpr (!Q) {
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+          Ks[n2] = cnt_s[warp * 8 + n2];
+          bs[n2] = base_s[warp * 8 + n2];
+        }
+      }
 #pragma unroll
       for (int n2 = 0; n2 < 8; ++n2) {
-        const int K = cnt_s[warp * 8 + n2];
-        const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (base_s[warp * 8 + n2] >> 1) + lane;
-        const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (base_s[warp * 8 + n2] >> 1) + lane;
+        const int K = Q ? cnt_s[warp * 8 + n2] : Ks[n2];
+        const int bse = Q ? base_s[warp * 8 + n2] : bs[n2];
+        const uint32_t* ea2 = reinterpret_cast<const uint32_t*>(ent_a) + (bse >> 1) + lane;
+        const float2* ew2 = reinterpret_cast<const float2*>(ent_w) + (bse >> 1) + lane;
         float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
 #pragma unroll 2
         for (int k = 0; k < K; k += 2) {  // the imaging kernel's entry pairs, in the same order
