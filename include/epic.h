@@ -106,6 +106,9 @@ typedef struct {
   int transforms_per_image;  /* transforms per (sample, channel, polarisation):
                                 4 when a 128 x 128 grid is folded into 64 x 64
                                 parity problems, else 1                          */
+  unsigned unpack_warps;     /* FP32 path at 64 x 64: bit w set for the four warps
+                                that unpack each next sample while the others
+                                still grid (chosen from the gather tables), or 0 */
 } epic_plan_info;
 
 /* Host-only check of a descriptor, no CUDA call (the same checks that

@@ -404,6 +404,7 @@ epic_status epic_plan_query(const epic_plan* h, epic_plan_info* info) {
   info->cluster_dim = (p.xform == EPIC_XFORM_FFT_FP32 && p.N == 128 && p.vq == 1) ? 2 : 1;
   info->transform_n = p.vq == 4 ? p.N / 2 : (p.xform != EPIC_XFORM_FFT_FP32 ? 64 : p.N);
   info->transforms_per_image = p.vq;
+  info->unpack_warps = p.unpack_warps;
   return EPIC_OK;
 }
 

@@ -18,6 +18,8 @@
 // (c, t) units (channel-major) and writes one partial image per channel it
 // touches; a separate kernel sums partials in CTA order and removes the
 // autocorrelation term.
+#include <algorithm>
+
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -120,11 +122,18 @@ __device__ __forceinline__ void fft_line(float2 (&v)[8], const float2 (&tw)[8], 
 
 // Shared-memory layout of the imaging kernel, in bytes from the base.
 struct FftSmem {
-  size_t R, scr, wst, coef, E, autos, ent_a, ent_w, total;
+  size_t R, scr, wst, coef, E, E2, autos, ent_a, ent_w, total;
 };
 
+// The 64 x 64 two-polarisation kernel with one antenna per thread can unpack
+// each next sample early, on the four warps whose gather is lightest (chosen at
+// plan time from the gather tables), into a second field buffer (see
+// fft_image_kernel and choose_unpack_warps).
+template <int N, int P, bool Q, int KA>
+constexpr bool kEarlyUnpack = N == 64 && P == 2 && !Q && KA == 1;
+
 template <int N, int P>
-__host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int ent_in_smem) {
+__host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int ent_in_smem, bool two_e = false) {
   using G = Geo<N>;
   FftSmem L;
   size_t o = 0;
@@ -138,6 +147,7 @@ __host__ __device__ inline FftSmem fft_smem_layout(int A, int max_entries, int e
   L.wst = take(sizeof(int) * 2 * (G::THREADS / 32) * 8);
   L.coef = take(sizeof(float2) * A * P);
   L.E = take((P == 2 ? 16 : 8) * (size_t)(A + 1));
+  L.E2 = two_e ? take((P == 2 ? 16 : 8) * (size_t)(A + 1)) : L.E;
   L.autos = take(sizeof(int4) * A);
   L.ent_a = take(ent_in_smem ? sizeof(uint16_t) * (size_t)max_entries : 0);
   L.ent_w = take(ent_in_smem ? sizeof(float) * (size_t)max_entries : 0);
@@ -162,7 +172,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
                      const float2* __restrict__ coef, const int* __restrict__ g_cnt, const int* __restrict__ g_base,
                      const int* __restrict__ g_off, const uint16_t* __restrict__ g_ent_a,
                      const float* __restrict__ g_ent_w, int max_entries, int ent_in_smem,
-                     const float2* __restrict__ twiddle, float* __restrict__ part, int* __restrict__ part_auto) {
+                     const float2* __restrict__ twiddle, float* __restrict__ part, int* __restrict__ part_auto,
+                     unsigned unpack_warps) {
   using G = Geo<N>;
   constexpr int NT = G::THREADS, NN = N * N, R1 = G::R1, HALF = N / 2;
   constexpr int MAXK = KA;
@@ -170,7 +181,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
 
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int WARPS = NT / 32;
-  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem);
+  const bool kEarly = kEarlyUnpack<N, P, Q, KA> && unpack_warps != 0u;
+  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem, kEarly);
   float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
   float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
   int* cnt_s = reinterpret_cast<int*>(smem + L.wst);    // [warps][8] trip counts
@@ -178,6 +190,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
   float2* coef_s = reinterpret_cast<float2*>(smem + L.coef);
   float4* E4 = reinterpret_cast<float4*>(smem + L.E);
   float2* E2 = reinterpret_cast<float2*>(smem + L.E);
+  float4* E4n = reinterpret_cast<float4*>(smem + L.E2);  // the next sample's fields (early unpack)
   int4* auto_s = reinterpret_cast<int4*>(smem + L.autos);
   uint16_t* enta_s = reinterpret_cast<uint16_t*>(smem + L.ent_a);
   float* entw_s = reinterpret_cast<float*>(smem + L.ent_w);
@@ -220,6 +233,18 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     }
   };
   load_raw(cu, tu, raw);
+
+  // early unpack (kEarly): the four warps of unpack_warps, whose rows hold few
+  // gather entries, unpack the next sample of the same channel into E4n after
+  // their row transforms, while the other warps still gather; its raw bytes (up
+  // to four antennas per unpack thread, A <= 512) are requested at the start of
+  // the sample
+  const int warp_id = tid >> 5;
+  const bool uwarp = kEarly && ((unpack_warps >> warp_id) & 1u);
+  const int ut = __popc(unpack_warps & ((1u << warp_id) - 1u)) * 32 + (tid & 31);
+  constexpr int kUT = 32 * 4;  // unpack threads (four warps)
+  unsigned rawu[4] = {0u, 0u, 0u, 0u};
+  bool have_e = false;  // E4 already holds this sample's fields
 
   int cur_c = -1;
   const uint16_t* ent_a = g_ent_a;
@@ -279,8 +304,18 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
       __syncthreads();
     }
     if (u + 1 < u1) load_raw(cn, tn, raw_next);
+    const bool early_next = kEarly && u + 1 < u1 && cn == c;  // the next sample is unpacked early
+    if (early_next && uwarp) {
+      const uint8_t* bn = volts + ((size_t)tn * C + cn) * (size_t)A * P;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int a = ut + kUT * j;
+        if (a < A) rawu[j] = __ldg(reinterpret_cast<const unsigned short*>(bn) + a);
+      }
+    }
 
-    // 1. unpack, calibrate, exact integer self powers
+    // 1. unpack, calibrate, exact integer self powers (unless unpacked early)
+    if (!have_e) {
 #pragma unroll
     for (int k = 0; k < MAXK; ++k) {
       const int a = tid + k * NT;
@@ -305,6 +340,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
       }
     }
     __syncthreads();
+    }
 
     // 2. grid (gather, fixed order) and 3a. row transforms; thread (row y, n1)
     {
@@ -366,6 +402,26 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
         for (int s = 0; s < 8; ++s) Rrow[G::rowpos(n1, s, sw)] = v[p][s];
       }
     }
+    if (early_next && uwarp) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int a = ut + kUT * j;
+        if (a < A) {
+          const unsigned rb = rawu[j];
+          const int xr = nib_hi(rb & 0xffu), xi = nib_lo(rb & 0xffu);
+          const int yr = nib_hi(rb >> 8), yi = nib_lo(rb >> 8);
+          const float2 kx = coef_s[a * P], ky = coef_s[a * P + 1];
+          E4n[a] = make_float4(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr, ky.x * yr - ky.y * yi,
+                               ky.x * yi + ky.y * yr);
+          int4 au = auto_s[a];
+          au.x += xr * xr + xi * xi;
+          au.y += yr * yr + yi * yi;
+          au.z += xr * yr + xi * yi;
+          au.w += xi * yr - xr * yi;
+          auto_s[a] = au;
+        }
+      }
+    }
     __syncthreads();
 
     // 3b. column transforms and 4. products; thread (column k, m1)
@@ -399,6 +455,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     for (int k = 0; k < MAXK; ++k) raw[k] = raw_next[k];
     cu = cn;
     tu = tn;
+    if (early_next) {  // the next sample's fields are in E4n (written before the row barrier)
+      float4* t = E4;
+      E4 = E4n;
+      E4n = t;
+    }
+    have_e = early_next;
   }
   flush(cur_c);
 }
@@ -420,11 +482,12 @@ cudaError_t launch_image(const Plan& p, const uint8_t* d_volts, int T, const Wor
   if (p.A <= Geo<N>::THREADS)
     fft_image_kernel<N, P, Q, 1><<<ws.ctas, p.threads, p.smem, s>>>(
         d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-        p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
+        p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto,
+        p.unpack_warps);
   else
     fft_image_kernel<N, P, Q><<<ws.ctas, p.threads, p.smem, s>>>(
         d_volts, T, p.C, p.A, ws.W, ws.units, ws.spans, coef, p.gt.d_cnt, p.gt.d_base, p.gt.d_chan_off,
-        p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto);
+        p.gt.d_ent_a, p.gt.d_ent_w, p.gt.max_chan_entries, p.ent_in_smem, p.d_twiddle, part, part_auto, 0u);
   return cudaGetLastError();
 }
 
@@ -444,7 +507,9 @@ cudaError_t launch_image_any(const Plan& p, const uint8_t* d_volts, int T, const
 
 size_t smem_for(const Plan& p, int ent_in_smem) {
   const int me = p.gt.max_chan_entries;
-  if (p.N == 64 || p.vq == 4) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem).total
+  // the second field buffer of the early unpack
+  const bool two_e = p.unpack_warps != 0u;
+  if (p.N == 64 || p.vq == 4) return p.P == 2 ? fft_smem_layout<64, 2>(p.A, me, ent_in_smem, two_e).total
                                  : fft_smem_layout<64, 1>(p.A, me, ent_in_smem).total;
   return p.P == 2 ? fft_smem_layout<32, 2>(p.A, me, ent_in_smem).total
                   : fft_smem_layout<32, 1>(p.A, me, ent_in_smem).total;
@@ -583,7 +648,45 @@ cudaError_t launch_debug_transform(Plan& p, const uint8_t* d_volts, int T, int t
                    : run(debug_transform_kernel<32>, Geo<32>::THREADS, 32);
 }
 
+// The early unpack's four warps (fft_image_kernel): per warp, the largest over
+// channels of its padded gather steps (sum over its slots of the trip count);
+// the four cheapest warps unpack each next sample if even the costliest of them
+// gathers at most half as much as the costliest warp -- rows outside the
+// aperture leave that much slack -- else none does (0).  Only for the kernel
+// variant that has the early unpack (64 x 64, two polarisations, not folded,
+// A <= 512).
+unsigned choose_unpack_warps(const Plan& p) {
+  if (!(p.N == 64 && p.vq != 4 && p.P == 2 && p.A <= Geo<64>::THREADS)) return 0u;
+  constexpr int kW = Geo<64>::THREADS / 32;
+  std::vector<int> cnt((size_t)p.C * kW * 8);
+  if (cudaMemcpy(cnt.data(), p.gt.d_cnt, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return 0u;
+  long long cost[kW] = {};
+  for (int c = 0; c < p.C; ++c)
+    for (int w = 0; w < kW; ++w) {
+      long long k = 0;
+      for (int s = 0; s < 8; ++s) k += cnt[((size_t)c * kW + w) * 8 + s];
+      cost[w] = std::max(cost[w], k);
+    }
+  int order[kW];
+  for (int w = 0; w < kW; ++w) order[w] = w;
+  std::stable_sort(order, order + kW, [&](int a, int b) { return cost[a] < cost[b]; });
+  const long long worst = cost[order[kW - 1]];
+  if (2 * cost[order[3]] > worst) return 0u;
+  unsigned mask = 0u;
+  for (int i = 0; i < 4; ++i) mask |= 1u << order[i];
+  return mask;
+}
+
 cudaError_t fft_image_config(Plan& p, int* ctas_per_sm) {
+  p.unpack_warps = choose_unpack_warps(p);
+  if (p.unpack_warps != 0u) {
+    // the second field buffer must not push the gather tables out of shared memory
+    const unsigned keep = p.unpack_warps;
+    p.unpack_warps = 0u;
+    const bool fits_without = ent_fits(p);
+    p.unpack_warps = keep;
+    if (fits_without && !ent_fits(p)) p.unpack_warps = 0u;
+  }
   p.ent_in_smem = ent_fits(p) ? 1 : 0;
   p.smem = smem_for(p, p.ent_in_smem);
   const bool n64 = p.N == 64 || p.vq == 4;  // 128 x 128 grids folded into 64 x 64 problems

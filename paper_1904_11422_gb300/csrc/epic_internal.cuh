@@ -109,6 +109,7 @@ struct Plan {
 
   // imaging launch shape and its workspace (partial images per CTA span)
   int ctas = 0, threads = 0, spans = 0, ent_in_smem = 0;
+  unsigned unpack_warps = 0;  // FP32 64 x 64: the four warps that unpack each next sample early (0: none)
   int ctas_use = 0;  // CTAs an imaging launch may use (0: ctas); set by the batch autotuner
   size_t smem = 0;
   float* d_part = nullptr;      // [ctas][spans][4][N][N]

@@ -61,6 +61,7 @@ class epic_plan_info(ctypes.Structure):
         ("threads_per_cta", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
         ("workspace_bytes", ctypes.c_size_t), ("max_time", ctypes.c_longlong),
         ("cluster_dim", ctypes.c_int), ("transform_n", ctypes.c_int), ("transforms_per_image", ctypes.c_int),
+        ("unpack_warps", ctypes.c_uint),
     ]
 
 

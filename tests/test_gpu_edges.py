@@ -360,3 +360,24 @@ def test_stacked_antennas_on_clusters():
     got = gpu_image(w, plan=plan)
     plan.close()
     assert_close(got, oracle_image(w), 2)
+
+
+def test_early_unpack_chosen_where_rows_are_empty():
+    """The 64 x 64 FP32 kernel lets the four warps with the lightest gather unpack
+    each next sample while the others still grid, when the aperture leaves rows
+    empty (a compact array), and keeps the plain unpack when every row holds
+    antennas (a square array filling the grid); both images equal the oracle's."""
+    compact = synth.random_small(1903, n_ant=60, n_pol=2, n_chan=2, grid_n=64, support=5, n_time=6,
+                                 diameter_m=60.0)
+    square = synth.random_small(1904, n_ant=300, n_pol=2, n_chan=2, grid_n=64, support=5, n_time=6)
+    lam_min = synth.C_LIGHT / square.freq_hz.max()
+    half = 0.25 * lam_min * (64 - 5 - 3)  # boxes stay inside the grid at the highest channel
+    rng = np.random.default_rng(1905)
+    square.ant_xy = rng.uniform(-half, half, size=(300, 2))
+    for w, early in ((compact, True), (square, False)):
+        plan = epic.plan_for(w)
+        mask = plan.info["unpack_warps"]
+        assert (bin(mask).count("1") == 4) if early else mask == 0, (w.name, hex(mask))
+        got = gpu_image(w, plan=plan)
+        plan.close()
+        assert_close(got, oracle_image(w), 2)
