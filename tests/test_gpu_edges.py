@@ -367,7 +367,9 @@ def test_early_unpack_chosen_where_rows_are_empty():
     each next sample while the others still grid, when the aperture leaves rows
     empty (a compact array), and keeps the plain unpack when every row holds
     antennas (a square array filling the grid); both images equal the oracle's."""
-    compact = synth.random_small(1903, n_ant=60, n_pol=2, n_chan=2, grid_n=64, support=5, n_time=6,
+    # 3 x 201 units over at most 152 CTAs: four consecutive samples per CTA, so the
+    # early unpack runs, and some CTAs' spans cross a channel boundary
+    compact = synth.random_small(1903, n_ant=60, n_pol=2, n_chan=3, grid_n=64, support=5, n_time=201,
                                  diameter_m=60.0)
     square = synth.random_small(1904, n_ant=300, n_pol=2, n_chan=2, grid_n=64, support=5, n_time=6)
     lam_min = synth.C_LIGHT / square.freq_hz.max()
@@ -380,4 +382,4 @@ def test_early_unpack_chosen_where_rows_are_empty():
         assert (bin(mask).count("1") == 4) if early else mask == 0, (w.name, hex(mask))
         got = gpu_image(w, plan=plan)
         plan.close()
-        assert_close(got, oracle_image(w), 2)
+        assert_close(got, oracle_image(w, use_fft=True), 2)
