@@ -371,15 +371,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int a = tid; a < jp->A; a += kThreads) pa[a] = auto_s[a];
   };
 
-  // the two bytes of each of the thread's antennas (a = tid + 512 k < A <= 1024),
+  // the two bytes of each of the thread's antennas (a = ta + 512 k < A <= 1024),
   // prefetched one sample ahead so that the unpack never waits for HBM; packed
-  // as antenna tid in the low and antenna tid + 512 in the high half
+  // as antenna ta in the low and antenna ta + 512 in the high half.  ta is the
+  // thread index shifted by half a block, so that arrays of up to 256 antennas
+  // are unpacked by warps 8-15 and warp 0, which issues the products, is spared
+  // the unpack of the next sample
+  const int ta = (tid + kThreads / 2) & (kThreads - 1);
   auto load_raw = [&](int c, int t) -> unsigned {
     const int cr = q128 ? c >> 2 : c;
     const unsigned short* base =
         reinterpret_cast<const unsigned short*>(jp->volts + ((size_t)t * jp->C + cr) * (size_t)jp->A * 2);
-    unsigned r = tid < jp->A ? (unsigned)__ldg(base + tid) : 0u;
-    if (tid + kThreads < jp->A) r |= (unsigned)__ldg(base + tid + kThreads) << 16;
+    unsigned r = ta < jp->A ? (unsigned)__ldg(base + ta) : 0u;
+    if (ta + kThreads < jp->A) r |= (unsigned)__ldg(base + ta + kThreads) << 16;
     return r;
   };
   unsigned raw = 0, raw_next = 0;
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto unpack = [&](unsigned rw) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int a = tid + h * kThreads;
+      const int a = ta + h * kThreads;
       const unsigned rb = h ? rw >> 16 : rw & 0xffffu;
       if (a < jp->A) {
         const int xr = nib_hi(rb & 0xffu), xi = nib_lo(rb & 0xffu);
