@@ -838,12 +838,24 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
   };
 
   int cu = c_first, tu = (int)(u0 - (long long)c_first * T);  // unit u = (channel cu, sample tu)
+  // the raw bytes of antenna tid, prefetched one unit ahead
+  auto load_raw1 = [&](int cv, int ts) -> unsigned {
+    if (tid >= A) return 0u;
+    const uint8_t* base = volts + ((size_t)ts * C + (Q ? cv >> 2 : cv)) * (size_t)A * P;
+    if constexpr (P == 2)
+      return __ldg(reinterpret_cast<const unsigned short*>(base) + tid);
+    else
+      return __ldg(base + tid);
+  };
+  unsigned raw_pref = load_raw1(cu, tu);
   for (long long u = u0; u < u1; ++u) {
-    const int c = cu, t = tu;
+    const int c = cu;
     if (++tu == T) {
       tu = 0;
       ++cu;
     }
+    const unsigned raw = raw_pref;
+    if (u + 1 < u1) raw_pref = load_raw1(cu, tu);
     const int cr = Q ? c >> 2 : c;  // the plan's channel (c is a virtual channel when folded)
     if (c != cur_c) {
       if (cur_c >= 0) {
@@ -892,13 +904,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
     }
 
     // 1. unpack and calibrate with the call's coefficients (thread a = tid)
-    unsigned raw = 0;
     if (tid < A) {
-      const uint8_t* base = volts + ((size_t)t * C + cr) * (size_t)A * P;
-      if constexpr (P == 2)
-        raw = __ldg(reinterpret_cast<const unsigned short*>(base) + tid);
-      else
-        raw = __ldg(base + tid);
       const int xr = nib_hi(raw & 0xffu), xi = nib_lo(raw & 0xffu);
       const float2 kx = coef_s[tid * P];
       const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
