@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
 
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int WARPS = NT / 32;
-  const bool kEarly = kEarlyUnpack<N, P, Q, KA> && unpack_warps != 0u;
-  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem, kEarly);
+  const bool early = kEarlyUnpack<N, P, Q, KA> && unpack_warps != 0u;
+  const FftSmem L = fft_smem_layout<N, P>(A, max_entries, ent_in_smem, early);
   float2* Rbuf = reinterpret_cast<float2*>(smem + L.R);
   float2* scr = reinterpret_cast<float2*>(smem + L.scr) + (threadIdx.x >> 5) * G::SCR;
   int* cnt_s = reinterpret_cast<int*>(smem + L.wst);    // [warps][8] trip counts
@@ -234,13 +234,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
   };
   load_raw(cu, tu, raw);
 
-  // early unpack (kEarly): the four warps of unpack_warps, whose rows hold few
+  // early unpack: the four warps of unpack_warps, whose rows hold few
   // gather entries, unpack the next sample of the same channel into E4n after
   // their row transforms, while the other warps still gather; its raw bytes (up
   // to four antennas per unpack thread, A <= 512) are requested at the start of
   // the sample
   const int warp_id = tid >> 5;
-  const bool uwarp = kEarly && ((unpack_warps >> warp_id) & 1u);
+  const bool uwarp = early && ((unpack_warps >> warp_id) & 1u);
   const int ut = __popc(unpack_warps & ((1u << warp_id) - 1u)) * 32 + (tid & 31);
   constexpr int kUT = 32 * 4;  // unpack threads (four warps)
   unsigned rawu[4] = {0u, 0u, 0u, 0u};
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
       __syncthreads();
     }
     if (u + 1 < u1) load_raw(cn, tn, raw_next);
-    const bool early_next = kEarly && u + 1 < u1 && cn == c;  // the next sample is unpacked early
+    const bool early_next = early && u + 1 < u1 && cn == c;  // the next sample is unpacked early
     if (early_next && uwarp) {
       const uint8_t* bn = volts + ((size_t)tn * C + cn) * (size_t)A * P;
 #pragma unroll
@@ -317,29 +317,29 @@ __global__ void __launch_bounds__(Geo<N>::THREADS, N == 32 ? 4 : 1)
     // 1. unpack, calibrate, exact integer self powers (unless unpacked early)
     if (!have_e) {
 #pragma unroll
-    for (int k = 0; k < MAXK; ++k) {
-      const int a = tid + k * NT;
-      if (a < A) {
-        const int xr = nib_hi(raw[k] & 0xffu), xi = nib_lo(raw[k] & 0xffu);
-        const float2 kx = coef_s[a * P];
-        const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
-        int4 au = auto_s[a];
-        au.x += xr * xr + xi * xi;
-        if constexpr (P == 2) {
-          const int yr = nib_hi(raw[k] >> 8), yi = nib_lo(raw[k] >> 8);
-          const float2 ky = coef_s[a * P + 1];
-          const float2 ey = make_float2(ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
-          E4[a] = make_float4(ex.x, ex.y, ey.x, ey.y);
-          au.y += yr * yr + yi * yi;
-          au.z += xr * yr + xi * yi;
-          au.w += xi * yr - xr * yi;
-        } else {
-          E2[a] = ex;
+      for (int k = 0; k < MAXK; ++k) {
+        const int a = tid + k * NT;
+        if (a < A) {
+          const int xr = nib_hi(raw[k] & 0xffu), xi = nib_lo(raw[k] & 0xffu);
+          const float2 kx = coef_s[a * P];
+          const float2 ex = make_float2(kx.x * xr - kx.y * xi, kx.x * xi + kx.y * xr);
+          int4 au = auto_s[a];
+          au.x += xr * xr + xi * xi;
+          if constexpr (P == 2) {
+            const int yr = nib_hi(raw[k] >> 8), yi = nib_lo(raw[k] >> 8);
+            const float2 ky = coef_s[a * P + 1];
+            const float2 ey = make_float2(ky.x * yr - ky.y * yi, ky.x * yi + ky.y * yr);
+            E4[a] = make_float4(ex.x, ex.y, ey.x, ey.y);
+            au.y += yr * yr + yi * yi;
+            au.z += xr * yr + xi * yi;
+            au.w += xi * yr - xr * yi;
+          } else {
+            E2[a] = ex;
+          }
+          auto_s[a] = au;
         }
-        auto_s[a] = au;
       }
-    }
-    __syncthreads();
+      __syncthreads();
     }
 
     // 2. grid (gather, fixed order) and 3a. row transforms; thread (row y, n1)
